@@ -1,0 +1,218 @@
+"""ctypes wrapper of the plain FP64 CPU oracle (vemg_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the benchmark's
+CPU-baseline leg. The product path never imports this module.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+import scipy.sparse as sp
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "vemg_oracle.c")
+LIB = os.path.join(HERE, "liboracle.so")
+
+BC_NEUMANN = 0
+BC_DIRICHLET_TOP = 1
+STATUS = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ENOTCONV", 5: "EBREAKDOWN"}
+
+# the paper's smoothed-aggregation parameters (section 6)
+THETA = 0.01
+OMEGA_P = 2.0 / 3.0
+COARSE_MAX = 512
+MAX_LEVELS = 10
+
+
+def build_oracle(force: bool = False) -> str:
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+                               "-shared", "-fPIC", "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build_oracle()
+        L = C.CDLL(LIB)
+        dp, ip, u8p = C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_uint8)
+        L.or_setup.restype = C.c_void_p
+        L.or_setup.argtypes = [C.c_int, dp, C.c_int, ip, u8p, C.c_int, ip, C.c_int, C.c_double,
+                               C.c_double, C.c_int, C.c_int, C.c_int, ip]
+        L.or_free.argtypes = [C.c_void_p]
+        L.or_size.restype = C.c_long
+        L.or_size.argtypes = [C.c_void_p, C.c_char_p, C.c_int, C.c_int]
+        L.or_get_csr.argtypes = [C.c_void_p, C.c_char_p, C.c_int, C.c_int, ip, ip, dp]
+        L.or_get_int.argtypes = [C.c_void_p, C.c_char_p, C.c_int, C.c_int, ip]
+        L.or_solve.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_int, C.c_int, ip, dp, dp, dp, C.c_int]
+        L.or_precond.argtypes = [C.c_void_p, dp, dp]
+        L.or_spmv.argtypes = [C.c_void_p, dp, dp]
+        L.or_load.argtypes = [C.c_void_p, dp, dp]
+        L.or_vcycle.argtypes = [C.c_void_p, C.c_int, dp, dp]
+        L.or_sa_aggregate.argtypes = [C.c_int, ip, ip, dp, C.c_double, ip]
+        L.or_colour.argtypes = [C.c_int, ip, ip, ip]
+        L.or_locate_points.argtypes = [C.c_int, ip, dp, C.c_int, dp, ip, dp]
+        L.or_elem_stiffness.restype = C.c_double
+        L.or_elem_stiffness.argtypes = [dp, dp]
+        _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+class Problem:
+    """Oracle setup of one mesh: ordering, A, E~, E~^T A E~, and the two SA chains."""
+
+    def __init__(self, mesh, bc: int = BC_NEUMANN, theta=THETA, omega_p=OMEGA_P, coarse_max=COARSE_MAX,
+                 max_levels=MAX_LEVELS, natural_order=False):
+        L = lib()
+        self._keep = (_f64(mesh.xyz), _i32(mesh.tets), np.ascontiguousarray(mesh.tags, dtype=np.uint8),
+                      _i32(mesh.top_tris))
+        xyz, tets, tags, tris = self._keep
+        st = C.c_int(0)
+        self.h = L.or_setup(xyz.shape[0], _p(xyz, C.c_double), tets.shape[0], _p(tets, C.c_int),
+                            _p(tags, C.c_uint8), tris.shape[0], _p(tris, C.c_int), bc, theta, omega_p,
+                            coarse_max, max_levels, int(natural_order), C.byref(st))
+        if not self.h:
+            raise OracleError(f"or_setup failed: {STATUS.get(st.value, st.value)}")
+        self.bc = bc
+        self.n = self.size("n")
+        self.mtop = self.size("mtop")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_free(self.h)
+            self.h = None
+
+    def size(self, key, which=1, level=0) -> int:
+        return int(lib().or_size(self.h, key.encode(), which, level))
+
+    def csr(self, name, which=1, level=0) -> sp.csr_matrix:
+        shapes = {"A": (self.n, self.n), "E": (self.n, self.mtop), "ET": (self.mtop, self.n),
+                  "Ac": (self.mtop, self.mtop)}
+        if name in shapes:
+            nrow, ncol = shapes[name]
+        else:
+            nrow = self.size("lev.n", which, level)
+            ncol = nrow if name == "lev.A" else self.size("lev.n", which, level + 1)
+        nnz_key = {"A": "nnzA", "E": "nnzE", "ET": "nnzE", "Ac": "nnzAc", "lev.A": "lev.nnz",
+                   "lev.P": "lev.nnzP"}[name]
+        nnz = self.size(nnz_key, which, level)
+        rp = np.zeros(nrow + 1, np.int32)
+        ci = np.zeros(max(nnz, 1), np.int32)
+        v = np.zeros(max(nnz, 1), np.float64)
+        rc = lib().or_get_csr(self.h, name.encode(), which, level, _p(rp, C.c_int), _p(ci, C.c_int),
+                              _p(v, C.c_double))
+        if rc:
+            raise OracleError(f"no matrix {name}")
+        return sp.csr_matrix((v[:nnz], ci[:nnz], rp), shape=(nrow, ncol))
+
+    def ints(self, name, which=1, level=0) -> np.ndarray:
+        cnt = self.n if name in ("new2old", "tri_of") else self.size("lev.n", which, level)
+        out = np.zeros(cnt, np.int32)
+        rc = lib().or_get_int(self.h, name.encode(), which, level, _p(out, C.c_int))
+        if rc:
+            raise OracleError(f"no int array {name}")
+        return out
+
+    def nlev(self, which):
+        return self.size("nlev", which)
+
+    def level_sizes(self, which):
+        return [self.size("lev.n", which, l) for l in range(self.nlev(which))]
+
+    def load(self, f):
+        f = _f64(f)
+        b = np.zeros(self.n)
+        lib().or_load(self.h, _p(f, C.c_double), _p(b, C.c_double))
+        return b
+
+    def solve(self, b, tol=1e-8, maxit=1000, flexible=False, hist_len=1000):
+        b = _f64(b)
+        x = np.zeros(self.n)
+        it = C.c_int(0)
+        rr, tr = C.c_double(0), C.c_double(0)
+        hist = np.zeros(hist_len)
+        st = lib().or_solve(self.h, _p(b, C.c_double), _p(x, C.c_double), tol, maxit, int(flexible),
+                            C.byref(it), C.byref(rr), C.byref(tr), _p(hist, C.c_double), hist_len)
+        return dict(x=x, iters=it.value, relres=rr.value, true_relres=tr.value, status=STATUS[st],
+                    hist=hist[:min(it.value, hist_len)])
+
+    def nunk(self):
+        return self.n if self.bc == BC_NEUMANN else self.n - self.mtop
+
+    def precond(self, r):
+        r = _f64(r)
+        z = np.zeros(self.nunk())
+        lib().or_precond(self.h, _p(r, C.c_double), _p(z, C.c_double))
+        return z
+
+    def spmv(self, x):
+        x = _f64(x)
+        y = np.zeros(self.nunk())
+        lib().or_spmv(self.h, _p(x, C.c_double), _p(y, C.c_double))
+        return y
+
+    def vcycle(self, which, b):
+        b = _f64(b)
+        x = np.zeros_like(b)
+        lib().or_vcycle(self.h, which, _p(b, C.c_double), _p(x, C.c_double))
+        return x
+
+
+def sa_aggregate(A: sp.csr_matrix, theta=THETA):
+    A = A.tocsr()
+    A.sort_indices()
+    rp, ci, v = _i32(A.indptr), _i32(A.indices), _f64(A.data)
+    agg = np.zeros(A.shape[0], np.int32)
+    nagg = lib().or_sa_aggregate(A.shape[0], _p(rp, C.c_int), _p(ci, C.c_int), _p(v, C.c_double), theta,
+                                 _p(agg, C.c_int))
+    return nagg, agg
+
+
+def colour(A: sp.csr_matrix):
+    A = A.tocsr()
+    A.sort_indices()
+    rp, ci = _i32(A.indptr), _i32(A.indices)
+    col = np.zeros(A.shape[0], np.int32)
+    nc = lib().or_colour(A.shape[0], _p(rp, C.c_int), _p(ci, C.c_int), _p(col, C.c_int))
+    return nc, col
+
+
+def locate_points(tris, xyz, pts_xy):
+    tris, xyz, pts = _i32(tris), _f64(xyz), _f64(pts_xy)
+    out = np.zeros(pts.shape[0], np.int32)
+    w = np.zeros((pts.shape[0], 3))
+    lib().or_locate_points(tris.shape[0], _p(tris, C.c_int), _p(xyz, C.c_double), pts.shape[0],
+                           _p(pts, C.c_double), _p(out, C.c_int), _p(w, C.c_double))
+    return out, w
+
+
+def elem_stiffness(p4x3):
+    p = _f64(p4x3).reshape(4, 3)
+    K = np.zeros(16)
+    det = lib().or_elem_stiffness(_p(p, C.c_double), _p(K, C.c_double))
+    return det, K.reshape(4, 4)

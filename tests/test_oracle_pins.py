@@ -1,0 +1,433 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each test checks a closed form, an invariant, a
+textbook special case or a brute-force computation written independently with numpy/scipy.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from oracle import oracle as O
+from paper_0912_1976_gb300 import inputs as I
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+def _mesh(nx, nz, h0=0.01, zj=0.0, xyj=0.0, seed=3, flat=False):
+    d = I.depth_flat(h0) if flat else I.depth_sines(h0)
+    return I.make_mesh(nx, nx, nz, d, z_jitter=zj, xy_jitter=xyj, seed=seed)
+
+
+def _read_golden(name):
+    vals = {}
+    for line in open(f"{GOLDEN}/{name}"):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = line.split("=")
+            vals[k.strip()] = v.strip()
+    return vals
+
+
+# --------------------------------------------------------------------------------------------
+# paper parameters (section 6)
+
+def test_paper_parameters_golden():
+    g = _read_golden("paper_parameters.txt")
+    assert O.THETA == float(g["strength_threshold"])
+    assert abs(O.OMEGA_P - eval(g["prolongator_omega"])) == 0.0
+
+
+# --------------------------------------------------------------------------------------------
+# element matrices and assembly (section 3)
+
+def test_reference_tet_stiffness_closed_form():
+    # textbook P1 stiffness of the reference tetrahedron (0,0,0),(1,0,0),(0,1,0),(0,0,1)
+    det, K = O.elem_stiffness(np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]]))
+    ref = np.array([[3, -1, -1, -1], [-1, 1, 0, 0], [-1, 0, 1, 0], [-1, 0, 0, 1]]) / 6.0
+    assert det == 1.0
+    assert np.allclose(K, ref, rtol=0, atol=1e-15)
+
+
+def test_stretched_tet_stiffness_scaling():
+    # scaling z by s multiplies the z-derivative part by 1/s and the x,y part by s (section 3 A_eps)
+    p = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
+    s = 1e-3
+    q = p * np.array([1, 1, s])
+    _, K = O.elem_stiffness(q)
+    # gradients of the reference tet: l0 = 1-x-y-z, l1 = x, l2 = y, l3 = z (z-gradient scaled 1/s)
+    G = np.array([[-1, -1, -1 / s], [1, 0, 0], [0, 1, 0], [0, 0, 1 / s]])
+    ref = (s / 6.0) * G @ G.T
+    assert np.allclose(K, ref, rtol=1e-13, atol=0)
+
+
+def test_assembly_symmetry_nullspace_and_pattern():
+    m = _mesh(6, 4, zj=0.3)
+    P = O.Problem(m)
+    A = P.csr("A")
+    D = (A - A.T)
+    assert D.count_nonzero() == 0 or abs(D).max() == 0.0           # bitwise symmetric
+    assert abs(A @ np.ones(A.shape[0])).max() <= 1e-13 * abs(A).max()  # constants in the kernel
+    # Freudenthal/Kuhn triangulation: an interior vertex has 14 neighbours (15 entries per row)
+    n2o = P.ints("new2old")
+    nz = m.nz
+    k = n2o % (nz + 1)
+    col = n2o // (nz + 1)
+    i, j = col % (m.nx + 1), col // (m.nx + 1)
+    inner = (k > 0) & (k < nz) & (i > 0) & (i < m.nx) & (j > 0) & (j < m.ny)
+    rl = np.diff(A.indptr)
+    assert np.all(rl[inner] == 15)
+
+
+def test_neumann_spectrum_simple_zero_and_abar_spd():
+    m = _mesh(6, 3, zj=0.3)
+    P = O.Problem(m)
+    A = P.csr("A").toarray()
+    w = np.linalg.eigvalsh(A)
+    assert abs(w[0]) < 1e-12 * w[-1]           # one zero eigenvalue (constants)
+    assert w[1] > 1e-8 * w[-1]                 # and only one
+    Abar = A[P.mtop:, P.mtop:]
+    np.linalg.cholesky(Abar)                   # SPD (raises otherwise)
+
+
+def test_mass_integrates_polynomials():
+    # sum_i (M f)_i = integral of f for f in P1; flat box of depth h0: int 1 = h0, int z = -h0^2/2
+    h0 = 0.05
+    m = _mesh(5, 3, h0=h0, zj=0.3, flat=True)
+    P = O.Problem(m)
+    one = P.load(np.ones(m.n))
+    assert abs(one.sum() - h0) < 1e-15
+    z = P.load(m.xyz[:, 2])
+    assert abs(z.sum() - (-h0 * h0 / 2)) < 1e-15
+    x = P.load(m.xyz[:, 0])
+    assert abs(x.sum() - h0 * 0.5) < 1e-15
+
+
+def test_manufactured_solution_second_order():
+    """O(h^2) convergence of the P1 solution of -Laplace u = f, all-Neumann, on the flat thin box
+    (section 3), with u = cos(pi x) cos(pi y) cos(pi z / H)."""
+    h0 = 0.01
+    errs = []
+    for nx, nz in [(8, 4), (16, 8), (32, 16)]:
+        m = _mesh(nx, nz, h0=h0, flat=True)
+        P = O.Problem(m)
+        b = P.load(I.manufactured_f(m, h0))
+        r = P.solve(b, tol=1e-12)
+        assert r["status"] == "OK"
+        u = I.manufactured_u(m, h0)
+        e = r["x"] - u
+        Me = P.load(e)
+        e = e - Me.sum() / P.load(np.ones(m.n)).sum()        # fix the constant by the mass-weighted mean
+        errs.append(math.sqrt(e @ P.load(e)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert 1.8 < rates[-1] < 2.2, (errs, rates)
+
+
+# --------------------------------------------------------------------------------------------
+# condition numbers (section 4)
+
+def _cond_spd(M):
+    w = np.linalg.eigvalsh(M)
+    return w[-1] / w[0]
+
+
+def test_condition_number_scaling_with_aspect_ratio():
+    """Cond(A_eps) on the complement of constants grows like eps^-2, Cond(A_bar_eps) stays
+    bounded by 2 Cond(A_bar_0) (section 4). The mesh is rescaled: same nodes, depth eps."""
+    conds, condbar = [], []
+    eps_list = [1e-1, 1e-2, 1e-3]
+    for eps in eps_list:
+        m = _mesh(6, 4, h0=eps, zj=0.3, flat=True, seed=11)
+        P = O.Problem(m)
+        A = P.csr("A").toarray() * eps   # rescaled operator A_eps = (H / L^2) A_phys
+        w = np.linalg.eigvalsh(A)
+        conds.append(w[-1] / w[1])
+        condbar.append(_cond_spd(A[P.mtop:, P.mtop:]))
+    r1 = conds[1] / conds[0]
+    r2 = conds[2] / conds[1]
+    assert 50 < r1 < 150 and 80 < r2 < 120        # x100 per decade of eps
+    # A_0: the vertical part only; eps -> 0 limit of the rescaled matrix
+    assert max(condbar) / min(condbar) < 2.0
+
+
+# --------------------------------------------------------------------------------------------
+# vertical extrapolation E~ (section 5.4) and the Galerkin surface operator
+
+def _brute_force_locate(tris, xyz, pts):
+    """argmax over ALL triangles of the smallest barycentric coordinate, ties to the lowest index"""
+    a, b, c = xyz[tris[:, 0], :2], xyz[tris[:, 1], :2], xyz[tris[:, 2], :2]
+
+    def orient(p, q, r):
+        return (q[..., 0] - p[..., 0]) * (r[..., 1] - p[..., 1]) - (q[..., 1] - p[..., 1]) * (r[..., 0] - p[..., 0])
+
+    out = np.zeros(len(pts), np.int64)
+    W = np.zeros((len(pts), 3))
+    for k, p in enumerate(pts):
+        P = np.broadcast_to(p, a.shape)
+        area = orient(a, b, c)
+        la = orient(P, b, c) / area
+        lb = orient(a, P, c) / area
+        lc = (1.0 - la) - lb
+        mn = np.minimum(np.minimum(la, lb), lc)
+        t = int(np.flatnonzero(mn == mn.max())[0])
+        out[k] = t
+        W[k] = (la[t], lb[t], lc[t])
+    return out, W
+
+
+def test_location_equals_brute_force_on_jittered_surface():
+    m = _mesh(7, 3, zj=0.3, xyj=0.2, seed=21)
+    pts = m.xyz[:, :2]
+    tri, w = O.locate_points(m.top_tris, m.xyz, pts)
+    tb, wb = _brute_force_locate(m.top_tris, m.xyz, pts)
+    assert np.array_equal(tri, tb)
+    assert np.array_equal(w, wb)
+
+
+def test_extrapolation_extruded_is_column_injection():
+    m = _mesh(6, 5, zj=0.3)
+    P = O.Problem(m)
+    E = P.csr("E")
+    assert np.all(np.diff(E.indptr) == 1) and np.all(E.data == 1.0)
+    n2o = P.ints("new2old")
+    col_of_node = n2o // (m.nz + 1)                        # generator column of each internal node
+    top_col = col_of_node[:P.mtop]
+    assert np.array_equal(top_col[E.indices], col_of_node)   # same column as its top node
+    # E~^T r = column sums, exactly
+    r = np.random.default_rng(0).standard_normal(P.n)
+    cs = np.zeros(P.mtop)
+    order = np.argsort(top_col)
+    sums = np.zeros(top_col.max() + 1)
+    np.add.at(sums, col_of_node, r)
+    assert np.allclose(E.T @ r, sums[top_col], rtol=1e-14, atol=1e-14)
+
+
+def test_extrapolation_rows_are_barycentric():
+    m = _mesh(6, 4, zj=0.3, xyj=0.2, seed=5)
+    P = O.Problem(m)
+    E = P.csr("E")
+    rs = np.asarray(E.sum(axis=1)).ravel()
+    assert np.all(np.abs(rs - 1.0) <= 4e-16)
+    # reproduces linear functions of (x, y): E~ x_top = x at every node
+    n2o = P.ints("new2old")
+    xy = m.xyz[n2o, :2]
+    for c in range(2):
+        assert np.allclose(E @ xy[:P.mtop, c], xy[:, c], rtol=0, atol=1e-14)
+
+
+def _depth_weighted_2d_stiffness(m, mtop, old2new_top, depth_at):
+    """A_c closed form on extruded meshes: sum_T area_T Hbar_T grad(l_i).grad(l_j)."""
+    K = np.zeros((mtop, mtop))
+    for t in m.top_tris:
+        p = m.xyz[t, :2]
+        area2 = (p[1, 0] - p[0, 0]) * (p[2, 1] - p[0, 1]) - (p[1, 1] - p[0, 1]) * (p[2, 0] - p[0, 0])
+        G = np.array([[p[1, 1] - p[2, 1], p[2, 0] - p[1, 0]],
+                      [p[2, 1] - p[0, 1], p[0, 0] - p[2, 0]],
+                      [p[0, 1] - p[1, 1], p[1, 0] - p[0, 0]]]) / area2
+        hbar = depth_at[t].mean()
+        idx = old2new_top[t]
+        K[np.ix_(idx, idx)] += 0.5 * area2 * hbar * (G @ G.T)
+    return K
+
+
+@pytest.mark.parametrize("zj", [0.0, 0.3])
+def test_galerkin_surface_operator_closed_form(zj):
+    h0 = 0.01
+    m = _mesh(8, 6, h0=h0, zj=zj)
+    P = O.Problem(m)
+    n2o = P.ints("new2old")
+    o2n = np.empty_like(n2o)
+    o2n[n2o] = np.arange(P.n)
+    x, y = m.xyz[:, 0], m.xyz[:, 1]
+    H = I.depth_sines(h0)(x, y)
+    K = _depth_weighted_2d_stiffness(m, P.mtop, o2n, H)
+    Ac = P.csr("Ac").toarray()
+    assert np.abs(Ac - K).max() <= 1e-10 * np.abs(K).max()
+    assert np.array_equal(Ac, Ac.T)                       # exact symmetry
+    assert np.abs(Ac @ np.ones(P.mtop)).max() <= 1e-10 * np.abs(K).max()
+
+
+# --------------------------------------------------------------------------------------------
+# the exact identity of section 5.3 (Eq. E multigrid)
+
+def test_exact_inverse_identity():
+    m = _mesh(5, 3, h0=0.01, zj=0.3, xyj=0.2, seed=2)
+    P = O.Problem(m)
+    A = P.csr("A").toarray()
+    mt = P.mtop
+    Abar = A[mt:, mt:]
+    Ct = A[mt:, :mt]
+    E = np.vstack([np.eye(mt), -np.linalg.solve(Abar, Ct)])
+    S = E.T @ A @ E
+
+    def pinv_on_complement(M):
+        # inverse on the complement of constants: (M + s 1 1^T)^-1 projected, s > 0
+        k = M.shape[0]
+        Qk = np.eye(k) - np.ones((k, k)) / k
+        return Qk @ np.linalg.inv(M + np.trace(M) / k ** 2) @ Qk
+
+    Z = np.zeros((P.n, P.n - mt))
+    Z[mt:] = np.eye(P.n - mt)
+    Minv = E @ pinv_on_complement(S) @ E.T + Z @ np.linalg.solve(Abar, Z.T)
+    Apinv = pinv_on_complement(A)
+    Q = np.eye(P.n) - np.ones((P.n, P.n)) / P.n          # restrict to the complement of constants
+    assert np.abs(Q @ Minv @ Q - Apinv).max() <= 1e-8 * np.abs(Apinv).max()
+
+
+# --------------------------------------------------------------------------------------------
+# smoothed aggregation (section 5.1, section 6)
+
+def _lap1d(n):
+    return sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tocsr()
+
+
+def test_aggregates_on_a_path_are_connected_triples_or_pairs():
+    n = 30
+    nagg, agg = O.sa_aggregate(_lap1d(n))
+    assert sorted(set(agg.tolist())) == list(range(nagg))
+    sizes = np.bincount(agg)
+    assert sizes.min() >= 1 and sizes.max() <= 5
+    for a in range(nagg):
+        idx = np.flatnonzero(agg == a)
+        assert idx.max() - idx.min() == len(idx) - 1       # contiguous on the path
+
+
+def test_weak_couplings_never_aggregate():
+    # two decoupled 1D chains joined by couplings below the 0.01 threshold
+    n = 12
+    A = sp.block_diag([_lap1d(n), _lap1d(n)]).tolil()
+    for i in range(n):
+        A[i, n + i] = A[n + i, i] = -0.005 * 2
+    A = A.tocsr()
+    nagg, agg = O.sa_aggregate(A)
+    assert set(agg[:n]).isdisjoint(set(agg[n:]))
+
+
+def test_colouring_is_proper():
+    m = _mesh(6, 4, zj=0.3)
+    P = O.Problem(m)
+    for which in (0, 1):
+        for l in range(P.nlev(which)):
+            A = P.csr("lev.A", which, l)
+            col = P.ints("lev.colour", which, l)
+            r, c = A.nonzero()
+            off = r != c
+            assert np.all(col[r[off]] != col[c[off]])
+            assert col.max() + 1 == P.size("lev.ncolours", which, l)
+
+
+def test_hierarchy_invariants():
+    m = _mesh(12, 8, h0=1e-3, zj=0.3)
+    P = O.Problem(m)
+    for which in (0, 1):
+        for l in range(P.nlev(which) - 1):
+            A = P.csr("lev.A", which, l)
+            Pl = P.csr("lev.P", which, l)
+            Ac = P.csr("lev.A", which, l + 1)
+            agg = P.ints("lev.agg", which, l)
+            assert sorted(set(agg.tolist())) == list(range(Ac.shape[0]))
+            Acd = Ac.toarray()
+            assert np.array_equal(Acd, Acd.T)
+            ref = (Pl.T @ (A @ Pl)).toarray()
+            assert np.abs(Acd - ref).max() <= 1e-12 * np.abs(ref).max()
+            if which == 0:
+                # singular chain: A 1 = 0 and the filtered smoothing keeps constants, P 1 = 1
+                assert np.abs(Pl @ np.ones(Pl.shape[1]) - 1).max() <= 1e-9
+
+
+# --------------------------------------------------------------------------------------------
+# preconditioner and solver
+
+def test_vcycle_and_preconditioner_symmetric_positive():
+    m = _mesh(5, 3, h0=0.01, zj=0.3)
+    P = O.Problem(m, coarse_max=40)
+    n = P.n
+    Mz = np.stack([P.precond(e) for e in np.eye(n)], axis=1)
+    assert np.abs(Mz - Mz.T).max() <= 1e-10 * np.abs(Mz).max()
+    w = np.linalg.eigvalsh(0.5 * (Mz + Mz.T))
+    assert w[0] > -1e-10 * w[-1]
+    assert P.nlev(1) >= 2          # a real multilevel cycle, not only the direct solve
+
+
+def test_solve_matches_dense_bordered_system():
+    for zj, xyj in [(0.3, 0.0), (0.3, 0.2)]:
+        m = _mesh(8, 4, h0=1e-2, zj=zj, xyj=xyj, seed=9)
+        P = O.Problem(m)
+        b = I.normal_loads(P.n, 4)
+        r = P.solve(b, tol=1e-11, maxit=2000)   # the xy-jittered mesh has a round-off floor near 2e-13
+        assert r["status"] == "OK"
+        n2o = P.ints("new2old")
+        A = P.csr("A").toarray()
+        bi = b[n2o] - b.mean()
+        K = np.block([[A, np.ones((P.n, 1))], [np.ones((1, P.n)), np.zeros((1, 1))]])
+        xs = np.linalg.solve(K, np.concatenate([bi, [0.0]]))[:P.n]
+        x = r["x"][n2o]
+        assert np.linalg.norm(x - xs) <= 1e-9 * np.linalg.norm(xs)
+
+
+def test_dirichlet_top_solve_matches_dense():
+    m = _mesh(8, 4, h0=1e-2, zj=0.3, seed=9)
+    P = O.Problem(m, bc=O.BC_DIRICHLET_TOP)
+    b = I.normal_loads(P.n, 5)
+    r = P.solve(b, tol=1e-13, maxit=500)
+    assert r["status"] == "OK"
+    n2o = P.ints("new2old")
+    A = P.csr("A").toarray()
+    mt = P.mtop
+    xs = np.linalg.solve(A[mt:, mt:], b[n2o][mt:])
+    x = r["x"][n2o]
+    assert np.all(x[:mt] == 0.0)
+    assert np.linalg.norm(x[mt:] - xs) <= 1e-10 * np.linalg.norm(xs)
+
+
+def test_flexible_cg_same_solution():
+    m = _mesh(10, 6, h0=1e-3, zj=0.3)
+    P = O.Problem(m)
+    b = I.normal_loads(P.n, 1)
+    a = P.solve(b, tol=1e-12)
+    f = P.solve(b, tol=1e-12, flexible=True)
+    assert abs(a["iters"] - f["iters"]) <= 2
+    assert np.linalg.norm(a["x"] - f["x"]) <= 1e-9 * np.linalg.norm(a["x"])
+
+
+def _jacobi_pcg_iters(A, b, tol, maxit=20000):
+    d = A.diagonal()
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = r / d
+    z -= z.mean()
+    p = z.copy()
+    rz = r @ z
+    bn = np.linalg.norm(b)
+    for k in range(maxit):
+        q = A @ p
+        a = rz / (p @ q)
+        x += a * p
+        r -= a * q
+        if np.linalg.norm(r) <= tol * bn:
+            return k + 1
+        z = r / d
+        z -= z.mean()
+        rzn = r @ z
+        p = z + (rzn / rz) * p
+        rz = rzn
+    return maxit
+
+
+def test_iterations_independent_of_aspect_ratio():
+    """Section 6.2: with vertical lumping the convergence rate no longer depends on eps, while a
+    point preconditioner degrades as eps shrinks."""
+    its, jac = [], []
+    for eps in [1e-2, 1e-3, 1e-4]:
+        m = _mesh(16, 8, h0=eps, zj=0.3, seed=4)
+        P = O.Problem(m)
+        b = I.normal_loads(P.n, 2)
+        r = P.solve(b, tol=1e-8)
+        assert r["status"] == "OK"
+        its.append(r["iters"])
+        bi = b[P.ints("new2old")]
+        jac.append(_jacobi_pcg_iters(P.csr("A"), bi - bi.mean(), 1e-8))
+    assert max(its) <= 1.25 * min(its), its
+    assert jac[0] < jac[1] < jac[2] and jac[2] > 2 * jac[0], jac
