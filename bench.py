@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark: solves/s of the vertical-extrapolation multigrid PCG on one GB300.
+
+Workload: the 256 x 256 x 32 extruded thin mesh (2,179,617 nodes, 12,582,912 tets) with depth
+H = 1e-3 (1 + 0.5 sin 2 pi x sin 2 pi y) (aspect ratio 1e-3), interior nodes z-jittered by
++-0.3 layer thickness, all-Neumann, i.i.d. N(0, 1) nodal loads projected to zero mean, stop at
+relative residual 1e-8. A step is one complete solve (every Krylov iteration with its additive
+multigrid preconditioner) with the hierarchy resident on the device; the hierarchy is built once
+(its time is reported as setup_s). Inputs (A: 0.39 GB, hierarchy > 1 GB) are larger than L2.
+
+  python bench.py [--steps K] [--warmup W] [--precision fp64|fp32] [--impl vemg|reference]
+
+Under torchrun (N > 1), every rank solves its own right-hand sides on its own GPU (independent
+problems, no collective in the data path); value = solves of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "zjit256"
+RTOL = 1e-8
+METRIC = "solves/s at FP64 rel-res 1e-8"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="vemg", choices=["vemg", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-probe", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={device_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(num(r[2]) for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------------------------
+# the CPU oracle: the reference arm and the cpu_baseline leg
+
+def time_oracle(mesh, b, iters_full=None, sample_iters=None):
+    """Time the oracle as it stands on this host (single thread). If sample_iters is None, one
+    full solve; otherwise a solve truncated at sample_iters iterations, scaled to a full solve."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    P = O.Problem(mesh)
+    setup_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    if sample_iters is None:
+        r = P.solve(b, tol=RTOL)
+        dt = time.perf_counter() - t0
+        return dict(setup_s=setup_s, solve_s=dt, iters=r["iters"], relres=r["relres"], problem=P)
+    r = P.solve(b, tol=0.0, maxit=sample_iters)
+    dt = time.perf_counter() - t0
+    return dict(setup_s=setup_s, sample_s=dt, iters=r["iters"], problem=P)
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    from paper_0912_1976_gb300 import inputs as I
+    mesh = I.make_workload_mesh(args.workload)
+    from oracle import oracle as O
+    P = O.Problem(mesh)
+    b0 = I.normal_loads(mesh.n, 2000)
+    full = P.solve(b0, tol=RTOL)                  # iteration count of a full solve (warm-up)
+    I_full = full["iters"]
+    sample_iters = 3
+    times = []
+    for k in range(args.warmup + args.steps):
+        b = I.normal_loads(mesh.n, 2100 + k)
+        t0 = time.perf_counter()
+        P.solve(b, tol=0.0, maxit=sample_iters)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    # a solve truncated at m iterations applies the preconditioner m + 1 times (the cost that
+    # dominates an iteration) and a full solve of I iterations applies it I times
+    per_iter = sum(times) / (len(times) * (sample_iters + 1))
+    solve_s = per_iter * I_full
+    value = 1.0 / solve_s
+    sample = (f"{args.steps} solves of the {args.workload} workload truncated at {sample_iters} PCG "
+              f"iterations each, scaled to the {I_full} iterations of a full solve to rel-res {RTOL:g}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * solve_s,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, mesh.n),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "iters": I_full}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args, n):
+    return {"workload": f"{args.workload}: 256x256x32 extruded hex->6 tets, {n} nodes, eps 1e-3, z-jitter 0.3, "
+                        "all-Neumann, N(0,1) loads mean-zero, rtol 1e-8",
+            "precision": args.precision, "rhs_per_step": 1,
+            "l2": "inputs larger than L2 (A alone 0.39 GB; no flush needed)",
+            "parallelism": f"independent problems x{args.gpus}" if args.gpus > 1 else "single GPU"}
+
+
+# --------------------------------------------------------------------------------------------
+# the GPU path
+
+def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe):
+    """Time args.steps solves (device-resident inputs), then the same through the host-buffer
+    entry point, then (optionally) per-kernel-class probes."""
+    nb = len(B)
+    X = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def step(j):
+        _, info = V.vemg_solve(h, B[j % nb], X, rtol=RTOL, max_it=1000)
+        if info["status"] != "OK":
+            raise RuntimeError(f"solve did not converge: {info}")
+        return info
+
+    for j in range(args.warmup):
+        step(j)
+    l0 = V.vemg_kernel_launches(h)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    torch.cuda.nvtx.range_push("timed")
+    e0.record()
+    for j in range(args.steps):
+        infos.append(step(args.warmup + j))
+    e1.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    launches = V.vemg_kernel_launches(h) - l0
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    iters = [i["iters"] for i in infos]
+    out = {"value": ws * args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps, "iters": iters,
+           "true_relres_max": max(i["true_relres"] for i in infos),
+           "gdof_iter_per_s": ws * sum(n * it for it in iters) / (ms / 1000.0) / 1e9,
+           "gpu_launches": launches, "clocks": clocks}
+    # end to end: host buffers through vemg_solve_host, copies inside the timed region
+    bh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    xh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    bh.copy_(B[0].cpu())
+    bnp, xnp = bh.numpy(), xh.numpy()
+    V.vemg_solve_host(h, bnp, xnp, rtol=RTOL)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0.record()
+    for j in range(args.steps):
+        V.vemg_solve_host(h, bnp, xnp, rtol=RTOL)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    out["e2e"] = {"value": ws * args.steps / (ms_e2e / 1000.0), "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
+                  "d2h_bytes_per_step": 8 * n}
+    classes = {}
+    if probe:
+        kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "sor_fine": V.VEMG_PROBE_SOR_FINE, "sor_all": V.VEMG_PROBE_SOR,
+                 "residual": V.VEMG_PROBE_RESIDUAL}
+        for name, kind in kinds.items():
+            V.vemg_probe(h, kind)
+            for j in range(2):
+                step(j)
+            r = V.vemg_probe_read(h)
+            V.vemg_probe(h, V.VEMG_PROBE_NONE)
+            if r["launches"]:
+                classes[name] = {"launches_per_solve": r["launches"] / 2, "ms_per_solve": r["ms"] / 2,
+                                 "achieved_gbs": r["bytes"] / (r["ms"] / 1000.0) / 1e9,
+                                 "bytes_per_launch": r["bytes"] / r["launches"]}
+    out["classes"] = classes
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_0912_1976_gb300 import inputs as I
+    from paper_0912_1976_gb300 import vemg as V
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    mesh = I.make_workload_mesh(args.workload)
+    n = mesh.n
+    vm = V.Mesh.from_inputs(mesh)
+    nb = min(args.steps + args.warmup, 8)
+    B = [torch.from_numpy(I.normal_loads(n, 2000 + 97 * rank + j)).cuda() for j in range(nb)]
+
+    res = {}
+    order = [args.precision] + [p for p in ("fp32", "fp64") if p != args.precision]
+    for prec in order:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        A = V.vemg_assemble(vm)
+        h = V.vemg_setup(A, vm, V.vemg_default_options(
+            precision=V.VEMG_PREC_FP64 if prec == "fp64" else V.VEMG_PREC_FP32))
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        r = measure(args, h, B, n, ws, rank, local, dist, V, torch, probe=not args.no_probe)
+        r["setup_s"] = setup_s
+        r["hierarchy_bytes"] = V.vemg_hierarchy_bytes(h)
+        res[prec] = r
+        h.destroy()
+        A.free()
+        del h, A
+
+    head = res[args.precision]
+    hbm, peak_kind = peaks()
+    roofline = None
+    classes = head["classes"]
+    if classes:
+        dom = max((c for c in classes if c != "sor_all"), key=lambda c: classes[c]["ms_per_solve"])
+        c = classes[dom]
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": c["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                    "frac": c["achieved_gbs"] / hbm, "peak_source": f"{peak_kind} hbm_gbs (copy, burst)",
+                    "traffic": None, "classes": classes}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r = time_oracle(mesh, B[0].cpu().numpy())
+        cpu = {"value": 1.0 / r["solve_s"], "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"one full oracle solve of the {args.workload} workload ({r['iters']} iterations, "
+                         f"{r['solve_s']:.1f} s; oracle setup {r['setup_s']:.1f} s not counted)"}
+
+    if rank == 0:
+        other = [p for p in res if p != args.precision]
+        comparator = None
+        if "fp64" in res and args.precision != "fp64":
+            f = res["fp64"]
+            comparator = {"name": "plain FP64 PCG (same hierarchy, FP64 V-cycles)", "value": f["value"],
+                          "iters": f["iters"][0], "ms_per_step": f["ms_per_step"],
+                          "e2e": f["e2e"]["value"], "true_relres_max": f["true_relres_max"],
+                          "speedup_of_value": head["value"] / f["value"]}
+        line = {"metric": METRIC, "value": head["value"], "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f64 outer + f32 preconditioner",
+                "data": "synthetic", "config": workload_config(args, n),
+                "gdof_iter_per_s": head["gdof_iter_per_s"], "iters": head["iters"],
+                "true_relres_max": head["true_relres_max"], "setup_s": head["setup_s"],
+                "hierarchy_bytes": head["hierarchy_bytes"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": head["clocks"],
+                "plain_fp64_pcg": comparator}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * vemg.h -- C ABI of libvemg: a GB300 (sm_103a) solver for the P1 finite-element Poisson
+ * problem on thin (small aspect ratio) tetrahedral meshes, preconditioned by vertical-
+ * extrapolation multigrid, after Kramer, Cotter and Pain, "Solving the Poisson equation on
+ * small aspect ratio domains using unstructured meshes".
+ *
+ * Conventions shared by every entry point:
+ *   - Nodes are numbered by the caller ("caller order"). Vectors passed in and out (b, x, f) are
+ *     in caller order; the library permutes internally (top-surface nodes first, section 3,
+ *     Eqs. phi_decomposition and equation_decomposition).
+ *   - Arrays named *_dev are device pointers on the current CUDA device; arrays in vemg_mesh and
+ *     names ending in _host are host pointers. The caller owns every array it passes; the
+ *     library copies what it keeps. Objects the library returns (vemg_hierarchy, the arrays of a
+ *     vemg_csr filled by vemg_assemble) are owned by the library and freed by vemg_destroy /
+ *     vemg_csr_free.
+ *   - stream is a cudaStream_t (NULL = the legacy default stream). Setup synchronises the
+ *     stream; solves enqueue their work on it and synchronise it before returning (the
+ *     iteration count and status are host values).
+ *   - Every entry point returns a status code (VEMG_OK = 0). No C++ exception crosses the ABI.
+ *     On error, output arrays hold unspecified values unless stated otherwise.
+ *   - Device memory comes from the allocator installed with vemg_set_allocator (cudaMalloc
+ *     when none is installed).
+ *   - A hierarchy may be used by one host thread at a time.
+ */
+#ifndef VEMG_H
+#define VEMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define VEMG_OK 0
+#define VEMG_EINVAL 1      /* bad argument (null pointer, size, option out of range) */
+#define VEMG_EMESH 2       /* invalid mesh: non-positive tet volume, index out of range, no top
+                              nodes, top triangle with a non-top vertex, node outside the top
+                              surface's projection */
+#define VEMG_ENOMEM 3      /* the allocator returned NULL */
+#define VEMG_ENOTCONV 4    /* max_it reached; x holds the last iterate, info is filled */
+#define VEMG_EBREAKDOWN 5  /* CG breakdown: p^T A p <= 0, NaN or Inf in the iteration */
+#define VEMG_ETIMEOUT 6    /* a bounded device-side wait expired */
+#define VEMG_ECUDA 7       /* a CUDA runtime call failed */
+#define VEMG_EINTERNAL 8   /* an internal capacity was exceeded */
+
+/* node tags (bitmask), section 2.1: top surface, floor, coasts */
+#define VEMG_TAG_TOP 1
+#define VEMG_TAG_FLOOR 2
+#define VEMG_TAG_COAST 4
+
+/* boundary conditions, section 3: all-Neumann (constants are the nullspace, removed by mean
+   projection) or Dirichlet phi = 0 on the top surface (the matrix A_bar) */
+#define VEMG_NEUMANN 0
+#define VEMG_DIRICHLET_TOP 1
+
+/* precision of the preconditioner; the outer Krylov loop is always FP64 */
+#define VEMG_PREC_FP64 0   /* everything FP64, CG outer loop */
+#define VEMG_PREC_FP32 1   /* V-cycle values, vectors and arithmetic FP32, flexible CG outer loop */
+
+/* Tetrahedral mesh, HOST pointers (section 2.1, section 3).
+   xyz: n_nodes x 3 doubles (x, y, z), z up, top surface at the largest z of each column.
+   tets: n_tets x 4 node ids with positive orientation ((p1-p0).((p2-p0)x(p3-p0)) > 0).
+   tags: n_nodes bitmasks of VEMG_TAG_*.
+   top_tris: n_top_tris x 3 node ids (all tagged VEMG_TAG_TOP), counter-clockwise in (x, y);
+   the triangulation of the top surface used for vertical extrapolation (section 5.4). */
+typedef struct vemg_mesh {
+    int64_t n_nodes;
+    const double *xyz;
+    int64_t n_tets;
+    const int32_t *tets;
+    const uint8_t *tags;
+    int64_t n_top_tris;
+    const int32_t *top_tris;
+} vemg_mesh;
+
+/* Square CSR matrix, DEVICE pointers, rows sorted by column, 32-bit indices. */
+typedef struct vemg_csr {
+    int64_t n;
+    int64_t nnz;
+    int32_t *rowptr; /* n + 1 */
+    int32_t *col;    /* nnz */
+    double *val;     /* nnz */
+} vemg_csr;
+
+typedef struct vemg_options {
+    int bc;           /* VEMG_NEUMANN or VEMG_DIRICHLET_TOP */
+    int precision;    /* VEMG_PREC_FP64 or VEMG_PREC_FP32 */
+    double strength;  /* SA strong-coupling threshold, section 6: 0.01 */
+    double omega_p;   /* SA prolongator smoothing weight, section 6: 2/3 */
+    int coarse_max;   /* a level of at most this many rows is solved directly (dense) */
+    int max_levels;   /* per multigrid chain, at most 16 */
+} vemg_options;
+
+typedef struct vemg_info {
+    int iters;            /* CG iterations (matrix-vector products with A) */
+    int status;           /* VEMG_OK, VEMG_ENOTCONV or VEMG_EBREAKDOWN */
+    double relres;        /* ||r_k||_2 / ||b||_2 of the recursively updated residual */
+    double true_relres;   /* ||b - A x||_2 / ||b||_2 recomputed at exit */
+    double b_mean;        /* Neumann: the mean removed from b (0 for Dirichlet-top) */
+} vemg_info;
+
+typedef struct vemg_hierarchy vemg_hierarchy;
+
+/* Fill opts with the paper's parameters (section 6): strength 0.01, omega_p = 2/3, Neumann,
+   FP64, coarse_max = 512, max_levels = 10. */
+void vemg_default_options(vemg_options *opts);
+
+/* Assemble the P1 stiffness matrix A_ij = integral grad N_i . grad N_j in physical coordinates
+   (section 3, Eq. Ax=b; the paper's rescaled A_eps equals (H / L^2) A). A_out receives device
+   arrays allocated by the library, in caller order; release them with vemg_csr_free. Entries
+   are summed over elements in ascending element index. Returns VEMG_EMESH on a non-positive
+   volume or an out-of-range node id. Synchronises the stream. */
+int vemg_assemble(const vemg_mesh *mesh, vemg_csr *A_out, void *stream);
+
+/* Load vector b = M f (section 3, Eq. Ax=b): M_ij = integral N_i N_j, f given by its nodal values.
+   f_dev and b_dev are device arrays of n_nodes doubles in caller order. */
+int vemg_load(const vemg_mesh *mesh, const double *f_dev, double *b_dev, void *stream);
+
+/* Free the arrays of a matrix returned by vemg_assemble. */
+void vemg_csr_free(vemg_csr *A);
+
+/* Build the preconditioner hierarchy for A (caller order, device, as vemg_assemble returns it):
+   the top-first ordering, the vertical extrapolation operator E~ by column location on the top
+   triangulation (section 5.4), the surface operator E~^T A E~ (section 5.1, Eq. reduced AMG),
+   the Dirichlet-top block A_bar, and smoothed-aggregation chains on both (section 6), giving
+   the additive preconditioner of Eq. ourpreconditioner (section 5.5). Dirichlet-top builds
+   the A_bar chain only. *out is owned by the library. Synchronises the stream. */
+int vemg_setup(const vemg_csr *A, const vemg_mesh *mesh, const vemg_options *opts, void *stream,
+               vemg_hierarchy **out);
+
+/* Free a hierarchy and all its device memory. NULL is ignored. */
+void vemg_destroy(vemg_hierarchy *h);
+
+/* Solve A x = b by preconditioned CG (FP64 preconditioner) or flexible CG (FP32 preconditioner)
+   from x0 = 0 (section 6: the multigrid cycle is applied as a preconditioner within each CG
+   iteration). Neumann: b is projected to zero mean (info->b_mean), every preconditioned
+   residual is projected to zero mean, and x has zero mean. Dirichlet-top: top entries of b are
+   ignored and x = 0 on top nodes. Stops when ||r_k|| <= rtol ||b||; ||b|| = 0 gives x = 0 and
+   iters = 0. b_dev and x_dev are device arrays of n_nodes doubles (caller order) and may not
+   overlap. Returns info->status. Synchronises the stream. */
+int vemg_solve(vemg_hierarchy *h, const double *b_dev, double *x_dev, double rtol, int max_it,
+               vemg_info *info, void *stream);
+
+/* As vemg_solve with HOST arrays b_host and x_host (n_nodes doubles, caller order): copies b to
+   the device, solves, copies x back. Page-locked host memory gives asynchronous copies. */
+int vemg_solve_host(vemg_hierarchy *h, const double *b_host, double *x_host, double rtol, int max_it,
+                    vemg_info *info, void *stream);
+
+/* Solve k systems A X = B with one right-hand side per column: column c of B is
+   B_dev[c * ldb + i], i < n_nodes (caller order), and likewise X. Each column is an independent
+   CG/FCG run with its own step lengths and convergence test; a converged column is frozen.
+   infos has k entries. Returns VEMG_OK if every column converged, else the first non-OK
+   column status. */
+int vemg_solve_batch(vemg_hierarchy *h, int k, const double *B_dev, int64_t ldb, double *X_dev,
+                     int64_t ldx, double rtol, int max_it, vemg_info *infos, void *stream);
+
+/* Device bytes held by a hierarchy (operators, transfer operators, work vectors). */
+int vemg_hierarchy_bytes(const vemg_hierarchy *h, size_t *bytes);
+
+/* Install the device allocator used by every later allocation (NULL alloc restores cudaMalloc /
+   cudaFree). alloc(bytes, ctx) returns a device pointer or NULL; free(ptr, ctx) releases it.
+   Memory allocated before a change is released through the allocator that allocated it. */
+int vemg_set_allocator(void *(*alloc)(size_t bytes, void *ctx), void (*free_fn)(void *ptr, void *ctx),
+                       void *ctx);
+
+/* Human-readable name of a status code (static string). */
+const char *vemg_strerror(int status);
+
+/* ---- introspection and single steps (used by parity tests; all in the internal top-first
+   ordering of section 3, chain 0 = surface chain on E~^T A E~, chain 1 = A_bar chain) ---- */
+
+/* Sizes: key is one of "n", "mtop", "nnzA", "nnzE", "nnzAc", "nlev" (of the chain), "direct"
+   (coarsest level of the chain solved by the dense solve), "lev.n", "lev.nnz", "lev.nnzP",
+   "lev.ncolours" (of level `level` of the chain). *out = -1 if the item does not exist. */
+int vemg_get_size(const vemg_hierarchy *h, const char *key, int chain, int level, int64_t *out);
+
+/* Copy a CSR matrix to HOST arrays sized by vemg_get_size: name is "A" (internal order), "E"
+   (vertical extrapolation E~, n x mtop), "Ac" (E~^T A E~), "lev.A", "lev.P" (of a chain level). */
+int vemg_get_csr(const vemg_hierarchy *h, const char *name, int chain, int level, int32_t *rowptr_host,
+                 int32_t *col_host, double *val_host);
+
+/* Copy an integer array to HOST: "new2old" (n: caller id of each internal node), "tri_of" (n:
+   located top triangle of each internal node, -1 on top nodes), "lev.agg" (aggregate of each
+   node of a level), "lev.colour" (colour of each node of a level). */
+int vemg_get_int(const vemg_hierarchy *h, const char *name, int chain, int level, int32_t *out_host);
+
+/* y = A x on the unknowns of the hierarchy's boundary condition (internal order, device). */
+int vemg_spmv(vemg_hierarchy *h, const double *x_dev, double *y_dev, void *stream);
+
+/* z = M^-1 r, one application of the preconditioner of Eq. ourpreconditioner (internal order,
+   device, without the mean projection). */
+int vemg_precond(vemg_hierarchy *h, const double *r_dev, double *z_dev, void *stream);
+
+/* One V-cycle of chain `chain` from a zero initial guess on its finest level (device). */
+int vemg_vcycle(vemg_hierarchy *h, int chain, const double *b_dev, double *x_dev, void *stream);
+
+/* ---- measurement ---- */
+
+/* Number of CUDA kernels the solve path of this hierarchy has launched since setup (host count). */
+int vemg_kernel_launches(const vemg_hierarchy *h, int64_t *count);
+
+/* Kernel classes that vemg_probe can time. */
+#define VEMG_PROBE_NONE 0
+#define VEMG_PROBE_SPMV_A 1      /* q = A p of the outer Krylov loop */
+#define VEMG_PROBE_SOR 2         /* every multicolour SOR launch of both chains */
+#define VEMG_PROBE_RESIDUAL 3    /* every V-cycle residual launch */
+#define VEMG_PROBE_SOR_FINE 4    /* SOR launches on the finest level of the A_bar chain */
+
+/* Start timing one kernel class (VEMG_PROBE_NONE stops): every later launch of that class
+   records a CUDA event before and after itself on its stream. Resets the accumulated totals. */
+int vemg_probe(vemg_hierarchy *h, int kind);
+
+/* Read the totals accumulated since vemg_probe (synchronises the device): summed kernel time in
+   milliseconds, number of launches, and summed algorithmic bytes, i.e. for a sparse pass
+   nnz (value + index bytes) + rows (row pointer + vector reads and writes). */
+int vemg_probe_read(vemg_hierarchy *h, double *total_ms, int64_t *launches, double *algorithmic_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VEMG_H */

@@ -1,0 +1,862 @@
+// solve.cu -- the solve phase: preconditioned CG with the additive vertical-extrapolation
+// multigrid preconditioner (Kramer, Cotter and Pain, section 5.5, Eq. ourpreconditioner):
+//
+//   z = E~ V(E~^T A E~)(E~^T r) + [0; I] V(A_bar)([0; I]^T r)
+//
+// where V(.) is one smoothed-aggregation V-cycle (section 5.1, section 6: one forward SOR sweep
+// with omega = 1 before the coarse correction, one backward sweep after it), and CG projects the
+// constant nullspace out of every preconditioned residual (section 3). With an FP32 preconditioner
+// the outer loop is flexible CG (Notay's FCG(1)), since the preconditioner is then not exactly
+// symmetric (section 5.5 on nested inexact inner solves).
+//
+// Operators are sliced ELL in solve order (layout.cu); one thread per row, 32 rows per warp.
+// Reductions are deterministic (fixed grid, fixed order). One solve runs as three CUDA graphs:
+// the first iteration, a WHILE conditional node whose body is one further iteration (the
+// condition is set on the device from the residual norm), and the exit work.
+#include <math.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace vemg {
+
+static constexpr int kRedBlocks = 608;  // 4 x 152 SMs
+static constexpr int kRedThreads = 256;
+static constexpr int kSellBlock = 128;  // 4 slices per block
+
+// ------------------------------------------------------------------------------------------
+// launch accounting and opt-in kernel timing
+
+static thread_local int64_t *g_count = nullptr;
+static thread_local Probe *g_probe = nullptr;
+static constexpr int kProbePairs = 1024;
+
+#define SOLVE_LAUNCHED()         \
+    do {                         \
+        VEMG_CHECK_LAUNCH();     \
+        if (g_count) ++*g_count; \
+    } while (0)
+
+static void probe_flush(Probe &p) {
+    if (p.used == 0) return;
+    VEMG_CHECK_CUDA(cudaEventSynchronize(p.ev[2 * p.used - 1]));
+    for (int i = 0; i < p.used; ++i) {
+        float ms = 0.f;
+        VEMG_CHECK_CUDA(cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]));
+        p.total_ms += ms;
+        p.total_bytes += p.bytes[i];
+    }
+    p.launches += p.used;
+    p.used = 0;
+}
+
+struct ProbeScope {
+    Probe *p = nullptr;
+    cudaStream_t s;
+    double bytes;
+    ProbeScope(int kind, double bytes_, cudaStream_t s_) : s(s_), bytes(bytes_) {
+        if (g_probe && g_probe->kind == kind) {
+            p = g_probe;
+            if ((int)p->ev.size() < 2 * kProbePairs) {
+                p->ev.resize(2 * kProbePairs);
+                for (auto &e : p->ev) VEMG_CHECK_CUDA(cudaEventCreate(&e));
+                p->bytes.resize(kProbePairs);
+            }
+            VEMG_CHECK_CUDA(cudaEventRecord(p->ev[2 * p->used], s));
+        }
+    }
+    ~ProbeScope() noexcept(false) {
+        if (!p) return;
+        VEMG_CHECK_CUDA(cudaEventRecord(p->ev[2 * p->used + 1], s));
+        p->bytes[p->used] = bytes;
+        if (++p->used == kProbePairs) probe_flush(*p);
+    }
+};
+
+void probe_start(vemg_hierarchy *h, int kind) {
+    Probe &p = h->probe;
+    if (p.used) probe_flush(p);
+    p.kind = kind;
+    p.total_ms = p.total_bytes = 0.0;
+    p.launches = 0;
+}
+
+void probe_read(vemg_hierarchy *h, double *ms, int64_t *launches, double *bytes) {
+    Probe &p = h->probe;
+    probe_flush(p);
+    *ms = p.total_ms;
+    *launches = p.launches;
+    *bytes = p.total_bytes;
+}
+
+// Algorithmic bytes of a sliced-ELL pass: its stored entries (value + column index) once, the
+// per-row vector traffic once (x gathers are counted as one read of the x vector).
+static double sell_bytes(int64_t nnz, double vb, int64_t rows, double per_row) {
+    return (double)nnz * (vb + 4.0) + (double)rows * per_row;
+}
+
+// ------------------------------------------------------------------------------------------
+// sliced-ELL kernels
+
+// Dot product of one sliced-ELL row with x: entries are loaded kU at a time (column indices and
+// values first, then the gathers), so that a row costs two dependent memory round trips per kU
+// entries instead of two per entry. lim >= 0 skips columns >= lim.
+static constexpr int kU = 16;
+
+template <class VT, class XT, class AT>
+__device__ __forceinline__ AT sell_row(const int *__restrict__ col, const VT *__restrict__ v, int o, int w,
+                                       const XT *x, int lim) {
+    AT acc = 0;
+    for (int k0 = 0; k0 < w; k0 += kU) {
+        int c[kU];
+        VT a[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            int k = k0 + u;
+            c[u] = k < w ? __ldg(col + o + 32 * k) : 0;
+            a[u] = k < w ? __ldg(v + o + 32 * k) : (VT)0;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (k0 + u < w && (lim < 0 || c[u] < lim)) acc += (AT)a[u] * (AT)x[c[u]];
+    }
+    return acc;
+}
+
+// y = A x (add: y += A x) over the slices [s0, s1); accumulation in AT
+template <class VT, class XT, class YT, class AT>
+__global__ void __launch_bounds__(kSellBlock) k_sell_spmv(int s0, int s1, const int *__restrict__ row0,
+                                                          const int *__restrict__ nrow, const int *__restrict__ off,
+                                                          const int *__restrict__ width, const int *__restrict__ col,
+                                                          const VT *__restrict__ v, const XT *__restrict__ x,
+                                                          YT *__restrict__ y, int add) {
+    int s = s0 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (s >= s1 || lane >= nrow[s]) return;
+    AT acc = sell_row<VT, XT, AT>(col, v, off[s] + lane, width[s], x, -1);
+    int r = row0[s] + lane;
+    y[r] = add ? (YT)((AT)y[r] + acc) : (YT)acc;
+}
+
+// SOR (omega = 1) on the rows of one colour (slices [s0, s1)):
+// x_i = (b_i - sum_{j != i} A_ij x_j) / A_ii. lim >= 0: sweep from x = 0, entries with column
+// >= lim (colours not yet visited) are zero and skipped; lim == 0 needs no entries at all.
+template <class VT, class XT, class BT>
+__global__ void __launch_bounds__(kSellBlock) k_sell_sor(int s0, int s1, const int *__restrict__ row0,
+                                                         const int *__restrict__ nrow, const int *__restrict__ off,
+                                                         const int *__restrict__ width, const int *__restrict__ col,
+                                                         const VT *__restrict__ v, const VT *__restrict__ dinv,
+                                                         const BT *__restrict__ b, XT *x, int lim) {
+    int s = s0 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (s >= s1 || lane >= nrow[s]) return;
+    int r = row0[s] + lane;
+    XT acc = lim == 0 ? (XT)0 : sell_row<VT, XT, XT>(col, v, off[s] + lane, width[s], x, lim);
+    x[r] = ((XT)b[r] - acc) * (XT)dinv[r];
+}
+
+// r = b - D x - (A - D) x over all slices
+template <class VT, class XT, class BT>
+__global__ void __launch_bounds__(kSellBlock) k_sell_residual(int nsl, const int *__restrict__ row0,
+                                                              const int *__restrict__ nrow, const int *__restrict__ off,
+                                                              const int *__restrict__ width, const int *__restrict__ col,
+                                                              const VT *__restrict__ v, const VT *__restrict__ diag,
+                                                              const BT *__restrict__ b, const XT *__restrict__ x,
+                                                              XT *__restrict__ r) {
+    int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (s >= nsl || lane >= nrow[s]) return;
+    int i = row0[s] + lane;
+    XT acc = (XT)diag[i] * x[i] + sell_row<VT, XT, XT>(col, v, off[s] + lane, width[s], x, -1);
+    r[i] = (XT)b[i] - acc;
+}
+
+// x = G b for the dense coarsest inverse (one warp per row, FP64 accumulation)
+template <class XT, class BT>
+__global__ void k_dense_mv(int n, const double *__restrict__ Gm, const BT *__restrict__ b, XT *__restrict__ x) {
+    int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (row >= n) return;
+    double s = 0.0;
+    for (int k = lane; k < n; k += 32) s += Gm[(int64_t)row * n + k] * (double)b[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[row] = (XT)s;
+}
+
+// ------------------------------------------------------------------------------------------
+// launch wrappers
+
+template <class VT, class XT, class YT, class AT>
+static void sell_spmv(const Sell &S, const XT *x, YT *y, int add, cudaStream_t s) {
+    if (S.nslices == 0) return;
+    int64_t threads = (int64_t)S.nslices * 32;
+    k_sell_spmv<VT, XT, YT, AT><<<grid_for(threads, kSellBlock), kSellBlock, 0, s>>>(
+        0, S.nslices, S.row0, S.nrow, S.off, S.width, S.col, (const VT *)S.v, x, y, add);
+    SOLVE_LAUNCHED();
+}
+
+template <class XT, class BT>
+static void sor_sweep(const SLevel &L, const BT *b, XT *x, bool forward, bool from_zero, bool fine, cudaStream_t s) {
+    for (int cc = 0; cc < L.ncolours; ++cc) {
+        int c = forward ? cc : L.ncolours - 1 - cc;
+        int s0 = L.cslice[c], s1 = L.cslice[c + 1];
+        if (s1 == s0) continue;
+        int lim = from_zero ? L.crow[c] : -1;
+        int rows = L.crow[c + 1] - L.crow[c];
+        // stored entries of the colour (none when lim == 0), b / dinv / x-write per row, and one
+        // read of the level's x shared among the sweep's colours
+        double bytes = sell_bytes(lim == 0 ? 0 : L.cnnz[c], sizeof(XT), rows, 3.0 * sizeof(XT)) +
+                       (double)sizeof(XT) * L.n / L.ncolours;
+        ProbeScope ps(fine ? PROBE_SOR_FINE : PROBE_SOR, bytes, s);
+        int64_t threads = (int64_t)(s1 - s0) * 32;
+        k_sell_sor<XT, XT, BT><<<grid_for(threads, kSellBlock), kSellBlock, 0, s>>>(
+            s0, s1, L.A.row0, L.A.nrow, L.A.off, L.A.width, L.A.col, (const XT *)L.A.v, (const XT *)L.dinv, b, x, lim);
+        SOLVE_LAUNCHED();
+    }
+}
+
+template <class XT, class BT>
+static void residual(const SLevel &L, const BT *b, const XT *x, XT *r, cudaStream_t s) {
+    ProbeScope ps(PROBE_RESIDUAL, sell_bytes(L.A.nnz, sizeof(XT), L.n, 5.0 * sizeof(XT)), s);
+    int64_t threads = (int64_t)L.A.nslices * 32;
+    k_sell_residual<XT, XT, BT><<<grid_for(threads, kSellBlock), kSellBlock, 0, s>>>(
+        L.A.nslices, L.A.row0, L.A.nrow, L.A.off, L.A.width, L.A.col, (const XT *)L.A.v, (const XT *)L.diag, b, x, r);
+    SOLVE_LAUNCHED();
+}
+
+// V-cycle with a zero initial guess (section 5.1); b of level 0 may be FP64 (the outer residual)
+template <class XT, class BT>
+static void vcycle_level(const SChain &C, int l, const BT *b, XT *x, cudaStream_t s) {
+    const SLevel &L = C.lv[l];
+    const bool fine = C.is_bar && l == 0;
+    if (l == C.nlev - 1) {
+        if (C.direct) {
+            k_dense_mv<XT, BT><<<grid_for(C.nc, 8), 256, 0, s>>>(C.nc, C.G, b, x);
+            SOLVE_LAUNCHED();
+            return;
+        }
+        // coarsening stalled above the direct-solve size: one symmetric SOR pass
+        sor_sweep<XT, BT>(L, b, x, true, true, fine, s);
+        sor_sweep<XT, BT>(L, b, x, false, false, fine, s);
+        return;
+    }
+    sor_sweep<XT, BT>(L, b, x, true, true, fine, s);
+    residual<XT, BT>(L, b, x, (XT *)L.r, s);
+    const SLevel &N = C.lv[l + 1];
+    sell_spmv<XT, XT, XT, XT>(L.PT, (const XT *)L.r, (XT *)N.b, 0, s);
+    vcycle_level<XT, XT>(C, l + 1, (const XT *)N.b, (XT *)N.x, s);
+    sell_spmv<XT, XT, XT, XT>(L.P, (const XT *)N.x, x, 1, s);
+    sor_sweep<XT, BT>(L, b, x, false, false, fine, s);
+}
+
+// ------------------------------------------------------------------------------------------
+// deterministic block reductions: every block writes its partial sums, the last block to finish
+// adds them in block order (fixed grid, fixed order: the same bits on every run)
+
+enum {
+    S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_MU, S_BN, S_RN, S_FLAG, S_TOL, S_MAXIT, S_ITERS, S_CONT, S_ZERO, S_TRUE,
+    S_BMEAN, S_XMEAN, S_COUNT
+};
+enum { C_SPMV = 0, C_XR, C_Z, C_SUMB, C_PREP, C_SUMX, C_TRUE, C_COUNT };
+
+template <int NS>
+__device__ bool finish_block(double (&acc)[NS], double *part, unsigned *counter, double (&tot)[NS]) {
+    __shared__ double sh[NS][kRedThreads / 32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        double v = acc[s];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[s][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NS) {
+        double v = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) v += sh[threadIdx.x][w];
+        part[threadIdx.x * kRedBlocks + blockIdx.x] = v;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)(kRedBlocks - 1);
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        double v = 0.0;
+        for (int k = threadIdx.x; k < kRedBlocks; k += kRedThreads) v += __ldcg(part + s * kRedBlocks + k);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if (lane == 0) sh[s][warp] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        double v = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) v += sh[s][w];
+        tot[s] = v;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+struct SellArgs {
+    int nsl;
+    const int *row0, *nrow, *off, *width, *col;
+    const double *v;
+};
+
+static SellArgs sargs(const Sell &S) {
+    return SellArgs{S.nslices, S.row0, S.nrow, S.off, S.width, S.col, (const double *)S.v};
+}
+
+// q = A p over all slices and (p, q); the last block sets alpha = rz / pq
+__global__ void __launch_bounds__(kRedThreads) k_spmv_pq(SellArgs A, const double *__restrict__ p,
+                                                         double *__restrict__ q, double *sc, double *part,
+                                                         unsigned *ctr) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double acc[1] = {0.0};
+    for (int s = blockIdx.x * (kRedThreads / 32) + warp; s < A.nsl; s += kRedBlocks * (kRedThreads / 32)) {
+        if (lane < A.nrow[s]) {
+            int r = A.row0[s] + lane;
+            double qv = sell_row<double, double, double>(A.col, A.v, A.off[s] + lane, A.width[s], p, -1);
+            q[r] = qv;
+            acc[0] += p[r] * qv;
+        }
+    }
+    double tot[1];
+    if (!finish_block<1>(acc, part, ctr, tot) || threadIdx.x != 0) return;
+    double pq = tot[0];
+    sc[S_PQ] = pq;
+    if (sc[S_ZERO] != 0.0) sc[S_ALPHA] = 0.0;
+    else if (!(pq > 0.0)) {
+        sc[S_FLAG] = 1.0;
+        sc[S_ALPHA] = 0.0;
+    } else sc[S_ALPHA] = sc[S_RZ] / pq;
+}
+
+// x += alpha p, r -= alpha q; the last block sets ||r||, the iteration count and the continuation
+// test (and, inside the loop graph, the WHILE condition)
+__global__ void __launch_bounds__(kRedThreads) k_update_xr(int n, const double *__restrict__ p,
+                                                           const double *__restrict__ q, double *__restrict__ x,
+                                                           double *__restrict__ r, double *sc, double *part,
+                                                           unsigned *ctr, cudaGraphConditionalHandle handle,
+                                                           int use_cond) {
+    double a = sc[S_ALPHA];
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < n; i += kRedBlocks * kRedThreads) {
+        x[i] += a * p[i];
+        double ri = r[i] - a * q[i];
+        r[i] = ri;
+        acc[0] += ri * ri;
+    }
+    double tot[1];
+    if (!finish_block<1>(acc, part, ctr, tot) || threadIdx.x != 0) return;
+    double rn = sqrt(tot[0]);
+    sc[S_RN] = rn;
+    double it = sc[S_ZERO] != 0.0 ? 0.0 : sc[S_ITERS] + 1.0;
+    sc[S_ITERS] = it;
+    if (!(rn == rn)) sc[S_FLAG] = 1.0;
+    bool cont = sc[S_ZERO] == 0.0 && sc[S_FLAG] == 0.0 && rn > sc[S_TOL] * sc[S_BN] && it < sc[S_MAXIT];
+    sc[S_CONT] = cont ? 1.0 : 0.0;
+    if (use_cond) cudaGraphSetConditional(handle, cont ? 1u : 0u);
+}
+
+// z from the two branches (Neumann: top rows z = y_s, other rows z = E~ y_s + x_bar; Dirichlet-
+// top: z = x_bar) and the sums t0 = sum z, t1 = (r, z), t2 = sum r, t3 = (z, q), t4 = sum q.
+// The last block sets mu (mean of z), rz = (r, z - mu) and beta: first direction 0, CG
+// rz'/rz, FCG -(z - mu, q) / (p, q).
+template <class XT>
+__global__ void __launch_bounds__(kRedThreads) k_combine(int nu, int mtop, SellArgs E, const XT *__restrict__ ys,
+                                                         const XT *__restrict__ xb, double *__restrict__ z,
+                                                         const double *__restrict__ r, const double *__restrict__ q,
+                                                         int neumann, int flexible, int first, double inv_n,
+                                                         double *sc, double *part, unsigned *ctr) {
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < nu; i += kRedBlocks * kRedThreads) {
+        double zi;
+        if (i < mtop) {
+            zi = (double)ys[i];
+        } else if (mtop > 0) {
+            int qq = i - mtop, sl = qq >> 5, ln = qq & 31;
+            zi = sell_row<double, XT, double>(E.col, E.v, E.off[sl] + ln, E.width[sl], ys, -1) + (double)xb[qq];
+        } else {
+            zi = (double)xb[i];
+        }
+        z[i] = zi;
+        double ri = r[i];
+        acc[0] += zi;
+        acc[1] += ri * zi;
+        acc[2] += ri;
+        if (flexible && !first) {
+            double qi = q[i];
+            acc[3] += zi * qi;
+            acc[4] += qi;
+        }
+    }
+    double tot[5];
+    if (!finish_block<5>(acc, part, ctr, tot) || threadIdx.x != 0) return;
+    double mu = neumann ? tot[0] * inv_n : 0.0;
+    double rz = tot[1] - mu * tot[2];
+    double beta;
+    if (first) beta = 0.0;
+    else if (flexible) beta = -(tot[3] - mu * tot[4]) / sc[S_PQ];
+    else beta = rz / sc[S_RZ];
+    sc[S_MU] = mu;
+    sc[S_BETA] = beta;
+    sc[S_RZ] = rz;
+    if (!(rz == rz) || !(beta == beta)) sc[S_FLAG] = 1.0;
+}
+
+// p = (z - mu) + beta p
+__global__ void k_update_p(int n, const double *__restrict__ sc, const double *__restrict__ z, double *__restrict__ p) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double mu = sc[S_MU], beta = sc[S_BETA];
+    if (i < n) p[i] = (z[i] - mu) + beta * p[i];
+}
+
+// sum of a vector; the last block stores the mean in sc[slot]
+__global__ void __launch_bounds__(kRedThreads) k_mean(int n, const double *__restrict__ a, double inv_n, int slot,
+                                                      double *sc, double *part, unsigned *ctr) {
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < n; i += kRedBlocks * kRedThreads) acc[0] += a[i];
+    double tot[1];
+    if (!finish_block<1>(acc, part, ctr, tot) || threadIdx.x != 0) return;
+    sc[slot] = tot[0] * inv_n;
+}
+
+// b -= mean (Neumann), r = b, x = 0, p = 0, ||b||; the last block sets ||b|| and the zero flag
+__global__ void __launch_bounds__(kRedThreads) k_prepare(int n, int neumann, double *__restrict__ b,
+                                                         double *__restrict__ r, double *__restrict__ x,
+                                                         double *__restrict__ p, double *sc, double *part,
+                                                         unsigned *ctr) {
+    double mu = neumann ? sc[S_BMEAN] : 0.0;
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < n; i += kRedBlocks * kRedThreads) {
+        double bi = b[i] - mu;
+        b[i] = bi;
+        r[i] = bi;
+        x[i] = 0.0;
+        p[i] = 0.0;
+        acc[0] += bi * bi;
+    }
+    double tot[1];
+    if (!finish_block<1>(acc, part, ctr, tot) || threadIdx.x != 0) return;
+    double bn = sqrt(tot[0]);
+    sc[S_BN] = bn;
+    if (bn == 0.0) {
+        sc[S_ZERO] = 1.0;
+        sc[S_CONT] = 0.0;
+    }
+}
+
+__global__ void k_sub_scalar(int n, double *__restrict__ a, const double *__restrict__ sc, int slot) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] -= sc[slot];
+}
+
+// ||b - A x|| (true residual); the last block stores it
+__global__ void __launch_bounds__(kRedThreads) k_true_res(SellArgs A, const double *__restrict__ x,
+                                                          const double *__restrict__ b, double *sc, double *part,
+                                                          unsigned *ctr) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double acc[1] = {0.0};
+    for (int s = blockIdx.x * (kRedThreads / 32) + warp; s < A.nsl; s += kRedBlocks * (kRedThreads / 32)) {
+        if (lane < A.nrow[s]) {
+            int r = A.row0[s] + lane;
+            double d = b[r] - sell_row<double, double, double>(A.col, A.v, A.off[s] + lane, A.width[s], x, -1);
+            acc[0] += d * d;
+        }
+    }
+    double tot[1];
+    if (!finish_block<1>(acc, part, ctr, tot) || threadIdx.x != 0) return;
+    sc[S_TRUE] = sqrt(tot[0]);
+}
+
+// ------------------------------------------------------------------------------------------
+// the preconditioner: two independent V-cycles (the additive form of Eq. ourpreconditioner)
+// on two streams, joined by the kernel that forms z
+
+template <class XT>
+static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, cudaStream_t s) {
+    const SChain &B = h->sbar;
+    const bool neu = h->bc == VEMG_NEUMANN, flex = h->precision != VEMG_PREC_FP64;
+    const int mt = neu ? h->mtop : 0;
+    const XT *ys = nullptr;
+    if (neu) {
+        const SChain &S = h->ssurf;
+        VEMG_CHECK_CUDA(cudaEventRecord(h->ev_fork, s));
+        VEMG_CHECK_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        // surface branch: r_c = E~^T r accumulated in FP64, one V-cycle on E~^T A E~
+        sell_spmv<double, double, XT, double>(h->ETs, r, (XT *)S.lv[0].b, 0, h->side);
+        vcycle_level<XT, XT>(S, 0, (const XT *)S.lv[0].b, (XT *)S.lv[0].x, h->side);
+        VEMG_CHECK_CUDA(cudaEventRecord(h->ev_join, h->side));
+        ys = (const XT *)S.lv[0].x;
+    }
+    // additive smoother: one V-cycle on A_bar with the trailing part of r
+    vcycle_level<XT, double>(B, 0, r + mt, (XT *)B.lv[0].x, s);
+    if (neu) VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+    k_combine<XT><<<kRedBlocks, kRedThreads, 0, s>>>(h->nu, mt, sargs(h->Enon), ys, (const XT *)B.lv[0].x, z, r,
+                                                     h->q, neu, flex, first, 1.0 / (double)h->nu, h->scal,
+                                                     h->red + 5 * kRedBlocks * C_Z, h->ctr + C_Z);
+    SOLVE_LAUNCHED();
+}
+
+static void precond_solve_order(vemg_hierarchy *h, const double *r, double *z, int first, cudaStream_t s) {
+    if (h->precision == VEMG_PREC_FP32) precond_t<float>(h, r, z, first, s);
+    else precond_t<double>(h, r, z, first, s);
+}
+
+// q = A p of the outer loop, with (p, q) and alpha
+static void spmv_outer(vemg_hierarchy *h, const double *x, double *y, cudaStream_t s) {
+    ProbeScope ps(PROBE_SPMV_A, sell_bytes(h->Aop.nnz, 8.0, h->Aop.n, 24.0), s);   // p read twice, q write
+    k_spmv_pq<<<kRedBlocks, kRedThreads, 0, s>>>(sargs(h->Aop), x, y, h->scal, h->red + 5 * kRedBlocks * C_SPMV,
+                                                 h->ctr + C_SPMV);
+    SOLVE_LAUNCHED();
+}
+
+__global__ void k_init_scalars(double *sc, double tol, int maxit) {
+    for (int i = 0; i < S_COUNT; ++i) sc[i] = 0.0;
+    sc[S_TOL] = tol;
+    sc[S_MAXIT] = (double)maxit;
+    sc[S_CONT] = maxit > 0 ? 1.0 : 0.0;
+}
+
+__global__ void k_gather(int n, const int *__restrict__ idx, const double *__restrict__ src, double *__restrict__ dst) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[idx[i]];
+}
+
+__global__ void k_scatter_out(int nu, const int *__restrict__ caller_of, const int *__restrict__ tops, int ntop,
+                              const double *__restrict__ src, double *__restrict__ dst) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nu) dst[caller_of[i]] = src[i];
+    if (i < ntop) dst[tops[i]] = 0.0;
+}
+
+// entry of the loop graph: continue only if the first iteration asked for more
+__global__ void k_cond_init(const double *sc, cudaGraphConditionalHandle handle) {
+    cudaGraphSetConditional(handle, sc[S_CONT] != 0.0 ? 1u : 0u);
+}
+
+// ------------------------------------------------------------------------------------------
+// the iteration, shared by the plain stream path and graph capture
+
+struct Graphs {
+    cudaGraph_t gpre = nullptr, gloop = nullptr, gpost = nullptr;
+    cudaGraphExec_t pre = nullptr, loop = nullptr, post = nullptr;
+    cudaGraphConditionalHandle handle = 0;
+    int64_t k_pre = 0, k_body = 0, k_post = 0;
+};
+
+static double *part_of(vemg_hierarchy *h, int c) { return h->red + 5 * kRedBlocks * c; }
+
+static void phase_pre(vemg_hierarchy *h, cudaStream_t s) {
+    const bool neu = h->bc == VEMG_NEUMANN;
+    const int nu = h->nu;
+    if (neu) {
+        k_mean<<<kRedBlocks, kRedThreads, 0, s>>>(nu, h->b, 1.0 / (double)nu, S_BMEAN, h->scal, part_of(h, C_SUMB),
+                                                  h->ctr + C_SUMB);
+        SOLVE_LAUNCHED();
+    }
+    k_prepare<<<kRedBlocks, kRedThreads, 0, s>>>(nu, neu, h->b, h->r, h->x, h->p, h->scal, part_of(h, C_PREP),
+                                                 h->ctr + C_PREP);
+    SOLVE_LAUNCHED();
+    precond_solve_order(h, h->r, h->z, 1, s);
+    k_update_p<<<grid_for(nu, 256), 256, 0, s>>>(nu, h->scal, h->z, h->p);
+    SOLVE_LAUNCHED();
+}
+
+// q = A p, alpha, x and r updates, ||r||, continuation
+static void phase_step(vemg_hierarchy *h, cudaStream_t s, cudaGraphConditionalHandle hd, int use_cond) {
+    spmv_outer(h, h->p, h->q, s);
+    k_update_xr<<<kRedBlocks, kRedThreads, 0, s>>>(h->nu, h->p, h->q, h->x, h->r, h->scal, part_of(h, C_XR),
+                                                   h->ctr + C_XR, hd, use_cond);
+    SOLVE_LAUNCHED();
+}
+
+// new preconditioned residual and search direction
+static void phase_direction(vemg_hierarchy *h, cudaStream_t s) {
+    precond_solve_order(h, h->r, h->z, 0, s);
+    k_update_p<<<grid_for(h->nu, 256), 256, 0, s>>>(h->nu, h->scal, h->z, h->p);
+    SOLVE_LAUNCHED();
+}
+
+static void phase_post(vemg_hierarchy *h, cudaStream_t s) {
+    const bool neu = h->bc == VEMG_NEUMANN;
+    const int nu = h->nu;
+    if (neu) {
+        k_mean<<<kRedBlocks, kRedThreads, 0, s>>>(nu, h->x, 1.0 / (double)nu, S_XMEAN, h->scal, part_of(h, C_SUMX),
+                                                  h->ctr + C_SUMX);
+        SOLVE_LAUNCHED();
+        k_sub_scalar<<<grid_for(nu, 256), 256, 0, s>>>(nu, h->x, h->scal, S_XMEAN);
+        SOLVE_LAUNCHED();
+    }
+    k_true_res<<<kRedBlocks, kRedThreads, 0, s>>>(sargs(h->Aop), h->x, h->b, h->scal, part_of(h, C_TRUE),
+                                                  h->ctr + C_TRUE);
+    SOLVE_LAUNCHED();
+}
+
+static void build_graphs(vemg_hierarchy *h) {
+    Graphs *G = new Graphs();
+    h->graphs = G;
+    cudaStream_t cs;
+    VEMG_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    Probe *saved = g_probe;
+    g_probe = nullptr;
+    int64_t *saved_count = g_count;
+    int64_t count = 0;
+    g_count = &count;
+    try {
+        // first iteration
+        VEMG_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        phase_pre(h, cs);
+        phase_step(h, cs, 0, 0);
+        VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &G->gpre));
+        G->k_pre = count;
+        // loop graph: a kernel that sets the condition, then the WHILE node whose body is one
+        // further iteration
+        count = 0;
+        VEMG_CHECK_CUDA(cudaGraphCreate(&G->gloop, 0));
+        VEMG_CHECK_CUDA(cudaGraphConditionalHandleCreate(&G->handle, G->gloop, 0, cudaGraphCondAssignDefault));
+        VEMG_CHECK_CUDA(cudaStreamBeginCaptureToGraph(cs, G->gloop, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        k_cond_init<<<1, 1, 0, cs>>>(h->scal, G->handle);
+        SOLVE_LAUNCHED();
+        cudaGraph_t captured = G->gloop;
+        VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &captured));
+        cudaGraphNode_t init_node;
+        size_t nn = 1;
+        VEMG_CHECK_CUDA(cudaGraphGetNodes(G->gloop, &init_node, &nn));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = G->handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        VEMG_CHECK_CUDA(cudaGraphAddNode(&cnode, G->gloop, &init_node, nullptr, 1, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        VEMG_CHECK_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        phase_direction(h, cs);
+        phase_step(h, cs, G->handle, 1);
+        VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &body));
+        G->k_body = count - 1;   // k_cond_init runs once per solve
+        G->k_pre += 1;
+        // exit work
+        count = 0;
+        VEMG_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        phase_post(h, cs);
+        VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &G->gpost));
+        G->k_post = count;
+        VEMG_CHECK_CUDA(cudaGraphInstantiate(&G->pre, G->gpre, 0));
+        VEMG_CHECK_CUDA(cudaGraphInstantiate(&G->loop, G->gloop, 0));
+        VEMG_CHECK_CUDA(cudaGraphInstantiate(&G->post, G->gpost, 0));
+    } catch (...) {
+        cudaStreamDestroy(cs);
+        g_probe = saved;
+        g_count = saved_count;
+        release_graphs(h);
+        throw;
+    }
+    g_probe = saved;
+    g_count = saved_count;
+    VEMG_CHECK_CUDA(cudaStreamDestroy(cs));
+}
+
+void release_graphs(vemg_hierarchy *h) {
+    Graphs *G = h->graphs;
+    if (G) {
+        if (G->pre) cudaGraphExecDestroy(G->pre);
+        if (G->loop) cudaGraphExecDestroy(G->loop);
+        if (G->post) cudaGraphExecDestroy(G->post);
+        if (G->gpre) cudaGraphDestroy(G->gpre);
+        if (G->gloop) cudaGraphDestroy(G->gloop);
+        if (G->gpost) cudaGraphDestroy(G->gpost);
+        delete G;
+        h->graphs = nullptr;
+    }
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    h->side = nullptr;
+    h->ev_fork = h->ev_join = nullptr;
+}
+
+void prepare_solve(vemg_hierarchy *h, cudaStream_t s) {
+    if (h->x) return;
+    Arena &ar = h->arena;
+    int n = h->n;
+    build_solve_layout(h, s);
+    h->x = ar.alloc<double>(n);
+    h->r = ar.alloc<double>(n);
+    h->z = ar.alloc<double>(n);
+    h->p = ar.alloc<double>(n);
+    h->q = ar.alloc<double>(n);
+    h->b = ar.alloc<double>(n);
+    h->red = ar.alloc<double>(5 * kRedBlocks * C_COUNT);
+    h->scal = ar.alloc<double>(S_COUNT);
+    h->ctr = ar.alloc<unsigned>(C_COUNT);
+    VEMG_CHECK_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(unsigned) * C_COUNT, s));
+    h->tops = ar.alloc<int>(h->mtop);
+    // caller ids of the top nodes (written as 0 by Dirichlet-top solves)
+    VEMG_CHECK_CUDA(cudaMemcpyAsync(h->tops, h->new2old, sizeof(int) * h->mtop, cudaMemcpyDeviceToDevice, s));
+    VEMG_CHECK_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    VEMG_CHECK_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    VEMG_CHECK_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+int solve(vemg_hierarchy *h, const double *b_in, double *x_out, double rtol, int max_it, vemg_info *info,
+          cudaStream_t s) {
+    prepare_solve(h, s);
+    const int nu = h->nu, B = 256;
+    const bool use_graph = h->probe.kind == PROBE_NONE;
+    g_probe = &h->probe;
+    g_count = &h->launches;
+    k_init_scalars<<<1, 1, 0, s>>>(h->scal, rtol, max_it);
+    SOLVE_LAUNCHED();
+    k_gather<<<grid_for(nu, B), B, 0, s>>>(nu, h->caller_of, b_in, h->b);
+    SOLVE_LAUNCHED();
+    double hs[S_COUNT];
+    if (use_graph) {
+        if (!h->graphs) build_graphs(h);
+        Graphs *G = h->graphs;
+        VEMG_CHECK_CUDA(cudaGraphLaunch(G->pre, s));
+        VEMG_CHECK_CUDA(cudaGraphLaunch(G->loop, s));
+        VEMG_CHECK_CUDA(cudaGraphLaunch(G->post, s));
+        VEMG_CHECK_CUDA(cudaMemcpyAsync(hs, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+        VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+        int it = (int)hs[S_ITERS];
+        h->launches += G->k_pre + G->k_post + (it > 1 ? (int64_t)(it - 1) * G->k_body : 0);
+    } else {
+        phase_pre(h, s);
+        phase_step(h, s, 0, 0);
+        for (;;) {
+            double cont = 0.0;
+            VEMG_CHECK_CUDA(cudaMemcpyAsync(&cont, h->scal + S_CONT, sizeof(double), cudaMemcpyDeviceToHost, s));
+            VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+            if (cont == 0.0) break;
+            phase_direction(h, s);
+            phase_step(h, s, 0, 0);
+        }
+        phase_post(h, s);
+        VEMG_CHECK_CUDA(cudaMemcpyAsync(hs, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+        VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    int ntop = h->bc == VEMG_DIRICHLET_TOP ? h->mtop : 0;
+    k_scatter_out<<<grid_for(std::max(nu, ntop), B), B, 0, s>>>(nu, h->caller_of, h->tops, ntop, h->x, x_out);
+    SOLVE_LAUNCHED();
+    VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+    info->iters = (int)hs[S_ITERS];
+    info->relres = hs[S_BN] > 0.0 ? hs[S_RN] / hs[S_BN] : 0.0;
+    info->true_relres = hs[S_BN] > 0.0 ? hs[S_TRUE] / hs[S_BN] : 0.0;
+    info->b_mean = hs[S_BMEAN];
+    int status;
+    if (hs[S_ZERO] != 0.0) status = VEMG_OK;
+    else if (hs[S_FLAG] != 0.0) status = VEMG_EBREAKDOWN;
+    else if (hs[S_RN] <= hs[S_TOL] * hs[S_BN]) status = VEMG_OK;
+    else status = VEMG_ENOTCONV;
+    info->status = status;
+    return status;
+}
+
+int solve_batch(vemg_hierarchy *h, int k, const double *B, int64_t ldb, double *X, int64_t ldx, double rtol,
+                int max_it, vemg_info *infos, cudaStream_t s) {
+    int rc = VEMG_OK;
+    for (int c = 0; c < k; ++c) {
+        int st = solve(h, B + (int64_t)c * ldb, X + (int64_t)c * ldx, rtol, max_it, &infos[c], s);
+        if (st != VEMG_OK && rc == VEMG_OK) rc = st;
+    }
+    return rc;
+}
+
+// ------------------------------------------------------------------------------------------
+// single steps in the internal (top-first) order, for the parity tests
+
+__global__ void k_perm_in(int n, const int *__restrict__ s2i, const double *__restrict__ a, double *__restrict__ b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[s2i[i]];
+}
+
+__global__ void k_perm_out(int n, const int *__restrict__ s2i, const double *__restrict__ a, double *__restrict__ b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[s2i[i]] = a[i];
+}
+
+// solve index -> internal index of the unknowns
+__global__ void k_solve_to_internal(int n, int off, const int *__restrict__ caller_of, const int *__restrict__ old2new,
+                                    int *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = old2new[caller_of[i]] - off;
+}
+
+void spmv_op(vemg_hierarchy *h, const double *x, double *y, cudaStream_t s) {
+    prepare_solve(h, s);
+    g_probe = &h->probe;
+    g_count = &h->launches;
+    int nu = h->nu, off = h->bc == VEMG_DIRICHLET_TOP ? h->mtop : 0;
+    Scratch<int> s2i(nu);
+    k_solve_to_internal<<<grid_for(nu, 256), 256, 0, s>>>(nu, off, h->caller_of, h->old2new, s2i);
+    SOLVE_LAUNCHED();
+    Scratch<double> xs(nu), ys(nu);
+    k_perm_in<<<grid_for(nu, 256), 256, 0, s>>>(nu, s2i, x, xs);
+    SOLVE_LAUNCHED();
+    spmv_outer(h, xs, ys, s);
+    k_perm_out<<<grid_for(nu, 256), 256, 0, s>>>(nu, s2i, ys, y);
+    SOLVE_LAUNCHED();
+    VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+void precond(vemg_hierarchy *h, const double *r, double *z, cudaStream_t s) {
+    prepare_solve(h, s);
+    g_probe = &h->probe;
+    g_count = &h->launches;
+    int nu = h->nu, off = h->bc == VEMG_DIRICHLET_TOP ? h->mtop : 0;
+    Scratch<int> s2i(nu);
+    k_solve_to_internal<<<grid_for(nu, 256), 256, 0, s>>>(nu, off, h->caller_of, h->old2new, s2i);
+    SOLVE_LAUNCHED();
+    Scratch<double> rs(nu), zs(nu);
+    k_perm_in<<<grid_for(nu, 256), 256, 0, s>>>(nu, s2i, r, rs);
+    SOLVE_LAUNCHED();
+    precond_solve_order(h, rs, zs, 1, s);
+    k_perm_out<<<grid_for(nu, 256), 256, 0, s>>>(nu, s2i, zs, z);
+    SOLVE_LAUNCHED();
+    VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+__global__ void k_perm_in_x(int n, const int *__restrict__ s2n, const double *__restrict__ a, void *b, int fp32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (fp32) ((float *)b)[i] = (float)a[s2n[i]];
+    else ((double *)b)[i] = a[s2n[i]];
+}
+
+__global__ void k_perm_out_x(int n, const int *__restrict__ s2n, const void *a, double *b, int fp32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    b[s2n[i]] = fp32 ? (double)((const float *)a)[i] : ((const double *)a)[i];
+}
+
+void vcycle(vemg_hierarchy *h, int chain, const double *b, double *x, cudaStream_t s) {
+    prepare_solve(h, s);
+    g_probe = &h->probe;
+    g_count = &h->launches;
+    const Chain &C = chain == 0 ? h->surf : h->bar;
+    const SChain &S = chain == 0 ? h->ssurf : h->sbar;
+    if (C.nlev == 0) throw Error{VEMG_EINVAL};
+    int n = C.lv[0].A.n;
+    bool f = S.fp32;
+    Scratch<char> bs((int64_t)n * 8), xs((int64_t)n * 8);
+    k_perm_in_x<<<grid_for(n, 256), 256, 0, s>>>(n, C.lv[0].crow, b, bs, f);
+    SOLVE_LAUNCHED();
+    if (f) vcycle_level<float, float>(S, 0, (const float *)bs.p, (float *)xs.p, s);
+    else vcycle_level<double, double>(S, 0, (const double *)bs.p, (double *)xs.p, s);
+    k_perm_out_x<<<grid_for(n, 256), 256, 0, s>>>(n, C.lv[0].crow, xs, x, f);
+    SOLVE_LAUNCHED();
+    VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace vemg
