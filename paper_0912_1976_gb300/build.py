@@ -22,6 +22,7 @@ UNITS = {
     "layout.cu": [],
     "solve.cu": [],
     "capi.cu": [],
+    "noalloc.cu": [],
 }
 
 

@@ -78,6 +78,7 @@ PROTOTYPES = {
     "vemg_spmv": (C.c_int, [_VP, _DP, _DP, _VP]),
     "vemg_precond": (C.c_int, [_VP, _DP, _DP, _VP]),
     "vemg_vcycle": (C.c_int, [_VP, C.c_int, _DP, _DP, _VP]),
+    "vemg_spmv_static": (C.c_int, [_VP, _DP, _DP, _VP]),
     "vemg_probe": (C.c_int, [_VP, C.c_int]),
     "vemg_kernel_launches": (C.c_int, [_VP, C.POINTER(C.c_int64)]),
     "vemg_probe_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
@@ -383,3 +384,11 @@ def vemg_kernel_launches(h: Hierarchy) -> int:
     v = C.c_int64()
     _check(lib().vemg_kernel_launches(h.h, C.byref(v)), "vemg_kernel_launches")
     return int(v.value)
+
+
+def vemg_spmv_static(h: Hierarchy, x_dev, y_dev=None, stream=None):
+    """y = A x with no device allocation (work buffers in the library's static device array)."""
+    if y_dev is None:
+        y_dev = torch.empty_like(x_dev)
+    _check(lib().vemg_spmv_static(h.h, _dev(x_dev), _dev(y_dev), _stream(stream)), "vemg_spmv_static")
+    return y_dev
