@@ -21,6 +21,7 @@ UNITS = {
     "setup.cu": ["-fmad=false"],
     "layout.cu": [],
     "solve.cu": [],
+    "batch.cu": [],
     "capi.cu": [],
     "noalloc.cu": [],
 }

@@ -191,6 +191,7 @@ int vemg_setup(const vemg_csr *A, const vemg_mesh *mesh, const vemg_options *opt
         if (h) {
             cudaStreamSynchronize((cudaStream_t)stream);
             release_graphs(h);
+            release_batch(h);
             h->arena.release();
             delete h;
         }
@@ -204,6 +205,7 @@ void vemg_destroy(vemg_hierarchy *h) {
     if (!h) return;
     cudaDeviceSynchronize();
     release_graphs(h);
+    release_batch(h);
     for (auto &e : h->probe.ev) cudaEventDestroy(e);
     h->arena.release();
     delete h;

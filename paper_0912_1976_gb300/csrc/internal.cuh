@@ -170,6 +170,7 @@ struct Chain {
 };
 
 struct Graphs;
+struct BatchWork;
 
 }  // namespace vemg
 
@@ -208,6 +209,7 @@ struct vemg_hierarchy {
     cudaStream_t side = nullptr;                  // second branch of the preconditioner
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     unsigned *ctr = nullptr;                      // arrival counters of the block reductions
+    vemg::BatchWork *batch = nullptr;             // multi-right-hand-side work (batch.cu)
 };
 
 namespace vemg {
@@ -220,6 +222,8 @@ void build_solve_layout(vemg_hierarchy *h, cudaStream_t s);
 // solve.cu
 void prepare_solve(vemg_hierarchy *h, cudaStream_t s);
 void release_graphs(vemg_hierarchy *h);
+// batch.cu
+void release_batch(vemg_hierarchy *h);
 int solve(vemg_hierarchy *h, const double *b, double *x, double rtol, int max_it, vemg_info *info,
           cudaStream_t s);
 int solve_batch(vemg_hierarchy *h, int k, const double *B, int64_t ldb, double *X, int64_t ldx, double rtol,

@@ -24,6 +24,8 @@ namespace vemg {
 static constexpr int kRedBlocks = 608;  // 4 x 152 SMs
 static constexpr int kRedThreads = 256;
 static constexpr int kSellBlock = 128;  // 4 slices per block
+static constexpr int kRows = 4;         // rows per thread and loop trip in the streaming kernels
+static constexpr int kEmax = 4;         // E~ rows with at most this many entries take the fast path
 
 // ------------------------------------------------------------------------------------------
 // launch accounting and opt-in kernel timing
@@ -348,11 +350,28 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(int n, const double *
                                                            int use_cond) {
     double a = sc[S_ALPHA];
     double acc[1] = {0.0};
-    for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < n; i += kRedBlocks * kRedThreads) {
-        x[i] += a * p[i];
-        double ri = r[i] - a * q[i];
-        r[i] = ri;
-        acc[0] += ri * ri;
+    constexpr int stride = kRedBlocks * kRedThreads;
+    for (int i0 = blockIdx.x * kRedThreads + threadIdx.x; i0 < n; i0 += kRows * stride) {
+        double pv[kRows], qv[kRows], xv[kRows], rv[kRows];
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+            int i = i0 + u * stride;
+            bool ok = i < n;
+            pv[u] = ok ? p[i] : 0.0;
+            qv[u] = ok ? q[i] : 0.0;
+            xv[u] = ok ? x[i] : 0.0;
+            rv[u] = ok ? r[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+            int i = i0 + u * stride;
+            if (i < n) {
+                x[i] = xv[u] + a * pv[u];
+                double ri = rv[u] - a * qv[u];
+                r[i] = ri;
+                acc[0] += ri * ri;
+            }
+        }
     }
     double tot[1];
     if (!finish_block<1>(acc, part, ctr, tot) || threadIdx.x != 0) return;
@@ -377,25 +396,54 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(int nu, int mtop, SellA
                                                          int neumann, int flexible, int first, double inv_n,
                                                          double *sc, double *part, unsigned *ctr) {
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < nu; i += kRedBlocks * kRedThreads) {
-        double zi;
-        if (i < mtop) {
-            zi = (double)ys[i];
-        } else if (mtop > 0) {
+    constexpr int stride = kRedBlocks * kRedThreads;
+    const bool dots_q = flexible && !first;
+    for (int i0 = blockIdx.x * kRedThreads + threadIdx.x; i0 < nu; i0 += kRows * stride) {
+        double zv[kRows], rv[kRows], qv[kRows];
+        // loads of every row first (the E~ row entries, x_bar, r, q), then the gathers of y_s
+        int ec[kRows][kEmax];
+        double ev[kRows][kEmax];
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+            int i = i0 + u * stride;
+            zv[u] = 0.0;
+            rv[u] = 0.0;
+            qv[u] = 0.0;
+#pragma unroll
+            for (int k = 0; k < kEmax; ++k) { ec[u][k] = -1; ev[u][k] = 0.0; }
+            if (i >= nu) continue;
+            rv[u] = r[i];
+            if (dots_q) qv[u] = q[i];
+            if (i < mtop) continue;
+            if (mtop == 0) { zv[u] = (double)xb[i]; continue; }
             int qq = i - mtop, sl = qq >> 5, ln = qq & 31;
-            zi = sell_row<double, XT, double>(E.col, E.v, E.off[sl] + ln, E.width[sl], ys, -1) + (double)xb[qq];
-        } else {
-            zi = (double)xb[i];
+            int o = E.off[sl] + ln, w = E.width[sl];
+            zv[u] = (double)xb[qq];
+            if (w <= kEmax) {
+#pragma unroll
+                for (int k = 0; k < kEmax; ++k)
+                    if (k < w) { ec[u][k] = __ldg(E.col + o + 32 * k); ev[u][k] = __ldg(E.v + o + 32 * k); }
+            } else {
+                zv[u] += sell_row<double, XT, double>(E.col, E.v, o, w, ys, -1);
+            }
         }
-        z[i] = zi;
-        double ri = r[i];
-        acc[0] += zi;
-        acc[1] += ri * zi;
-        acc[2] += ri;
-        if (flexible && !first) {
-            double qi = q[i];
-            acc[3] += zi * qi;
-            acc[4] += qi;
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+            int i = i0 + u * stride;
+            if (i >= nu) continue;
+            double zi = zv[u];
+            if (i < mtop) zi = (double)ys[i];
+#pragma unroll
+            for (int k = 0; k < kEmax; ++k)
+                if (ec[u][k] >= 0) zi += ev[u][k] * (double)ys[ec[u][k]];
+            z[i] = zi;
+            acc[0] += zi;
+            acc[1] += rv[u] * zi;
+            acc[2] += rv[u];
+            if (dots_q) {
+                acc[3] += zi * qv[u];
+                acc[4] += qv[u];
+            }
         }
     }
     double tot[5];
@@ -423,7 +471,14 @@ __global__ void k_update_p(int n, const double *__restrict__ sc, const double *_
 __global__ void __launch_bounds__(kRedThreads) k_mean(int n, const double *__restrict__ a, double inv_n, int slot,
                                                       double *sc, double *part, unsigned *ctr) {
     double acc[1] = {0.0};
-    for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < n; i += kRedBlocks * kRedThreads) acc[0] += a[i];
+    constexpr int stride = kRedBlocks * kRedThreads;
+    for (int i0 = blockIdx.x * kRedThreads + threadIdx.x; i0 < n; i0 += kRows * stride) {
+        double v[kRows];
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) v[u] = i0 + u * stride < n ? a[i0 + u * stride] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) acc[0] += v[u];
+    }
     double tot[1];
     if (!finish_block<1>(acc, part, ctr, tot) || threadIdx.x != 0) return;
     sc[slot] = tot[0] * inv_n;
@@ -436,13 +491,23 @@ __global__ void __launch_bounds__(kRedThreads) k_prepare(int n, int neumann, dou
                                                          unsigned *ctr) {
     double mu = neumann ? sc[S_BMEAN] : 0.0;
     double acc[1] = {0.0};
-    for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < n; i += kRedBlocks * kRedThreads) {
-        double bi = b[i] - mu;
-        b[i] = bi;
-        r[i] = bi;
-        x[i] = 0.0;
-        p[i] = 0.0;
-        acc[0] += bi * bi;
+    constexpr int stride = kRedBlocks * kRedThreads;
+    for (int i0 = blockIdx.x * kRedThreads + threadIdx.x; i0 < n; i0 += kRows * stride) {
+        double v[kRows];
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) v[u] = i0 + u * stride < n ? b[i0 + u * stride] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+            int i = i0 + u * stride;
+            if (i < n) {
+                double bi = v[u] - mu;
+                b[i] = bi;
+                r[i] = bi;
+                x[i] = 0.0;
+                p[i] = 0.0;
+                acc[0] += bi * bi;
+            }
+        }
     }
     double tot[1];
     if (!finish_block<1>(acc, part, ctr, tot) || threadIdx.x != 0) return;
@@ -761,16 +826,6 @@ int solve(vemg_hierarchy *h, const double *b_in, double *x_out, double rtol, int
     else status = VEMG_ENOTCONV;
     info->status = status;
     return status;
-}
-
-int solve_batch(vemg_hierarchy *h, int k, const double *B, int64_t ldb, double *X, int64_t ldx, double rtol,
-                int max_it, vemg_info *infos, cudaStream_t s) {
-    int rc = VEMG_OK;
-    for (int c = 0; c < k; ++c) {
-        int st = solve(h, B + (int64_t)c * ldb, X + (int64_t)c * ldx, rtol, max_it, &infos[c], s);
-        if (st != VEMG_OK && rc == VEMG_OK) rc = st;
-    }
-    return rc;
 }
 
 // ------------------------------------------------------------------------------------------
