@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--rhs", type=int, default=0,
+                    help="right-hand sides per step (0: the workload's own count); >1 uses vemg_solve_batch")
     return ap.parse_args()
 
 
@@ -168,9 +170,13 @@ def run_reference(args):
 
 
 def workload_config(args, n):
-    return {"workload": f"{args.workload}: 256x256x32 extruded hex->6 tets, {n} nodes, eps 1e-3, z-jitter 0.3, "
-                        "all-Neumann, N(0,1) loads mean-zero, rtol 1e-8",
-            "precision": args.precision, "rhs_per_step": 1,
+    from paper_0912_1976_gb300 import inputs as I
+    w = I.WORKLOADS[args.workload]
+    kr = args.rhs or w.get("nrhs", 1)
+    return {"workload": f"{args.workload}: {w['nx']}x{w['ny']}x{w['nz']} extruded hex->6 tets, {n} nodes, "
+                        f"H0 {w['depth'][1]:g}, z-jitter {w['z_jitter']}, xy-jitter {w['xy_jitter']}, "
+                        f"all-Neumann, N(0,1) loads mean-zero, rtol {RTOL:g}",
+            "precision": args.precision, "rhs_per_step": kr,
             "l2": "inputs larger than L2 (A alone 0.39 GB; no flush needed)",
             "parallelism": f"independent problems x{args.gpus}" if args.gpus > 1 else "single GPU"}
 
@@ -182,9 +188,17 @@ def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe):
     """Time args.steps solves (device-resident inputs), then the same through the host-buffer
     entry point, then (optionally) per-kernel-class probes."""
     nb = len(B)
-    X = torch.empty(n, dtype=torch.float64, device="cuda")
+    X = torch.empty_like(B[0])
+    batched = B[0].dim() == 2
+    kcols = B[0].shape[0] if batched else 1
 
     def step(j):
+        if batched:
+            _, infos = V.vemg_solve_batch(h, B[j % nb], X, rtol=RTOL, max_it=1000)
+            bad = [i for i in infos if i["status"] != "OK"]
+            if bad:
+                raise RuntimeError(f"batched solve did not converge: {bad[0]}")
+            return {"iters": max(i["iters"] for i in infos), "true_relres": max(i["true_relres"] for i in infos)}
         _, info = V.vemg_solve(h, B[j % nb], X, rtol=RTOL, max_it=1000)
         if info["status"] != "OK":
             raise RuntimeError(f"solve did not converge: {info}")
@@ -214,22 +228,35 @@ def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     iters = [i["iters"] for i in infos]
-    out = {"value": ws * args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps, "iters": iters,
+    out = {"value": ws * kcols * args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps, "iters": iters,
            "true_relres_max": max(i["true_relres"] for i in infos),
-           "gdof_iter_per_s": ws * sum(n * it for it in iters) / (ms / 1000.0) / 1e9,
+           "gdof_iter_per_s": ws * kcols * sum(n * it for it in iters) / (ms / 1000.0) / 1e9,
            "gpu_launches": launches, "clocks": clocks}
-    # end to end: host buffers through vemg_solve_host, copies inside the timed region
-    bh = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    xh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    # end to end: host buffers, host-to-device copy of the step's inputs and device-to-host copy
+    # of its results inside the timed region (vemg_solve_host for one right-hand side; pinned
+    # copies around vemg_solve_batch for a batch)
+    bh = torch.empty(B[0].shape, dtype=torch.float64, pin_memory=True)
+    xh = torch.empty(B[0].shape, dtype=torch.float64, pin_memory=True)
     bh.copy_(B[0].cpu())
     bnp, xnp = bh.numpy(), xh.numpy()
-    V.vemg_solve_host(h, bnp, xnp, rtol=RTOL)
+    Bd = torch.empty_like(B[0])
+
+    def e2e_step():
+        if batched:
+            Bd.copy_(bh, non_blocking=True)
+            V.vemg_solve_batch(h, Bd, X, rtol=RTOL, max_it=1000)
+            xh.copy_(X, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        else:
+            V.vemg_solve_host(h, bnp, xnp, rtol=RTOL)
+
+    e2e_step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e0.record()
     for j in range(args.steps):
-        V.vemg_solve_host(h, bnp, xnp, rtol=RTOL)
+        e2e_step()
     e1.record()
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1)
@@ -237,10 +264,10 @@ def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe):
         t = torch.tensor([ms_e2e], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_e2e = float(t.item())
-    out["e2e"] = {"value": ws * args.steps / (ms_e2e / 1000.0), "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
-                  "d2h_bytes_per_step": 8 * n}
+    out["e2e"] = {"value": ws * kcols * args.steps / (ms_e2e / 1000.0), "unit": "solves/s",
+                  "h2d_bytes_per_step": 8 * n * kcols, "d2h_bytes_per_step": 8 * n * kcols}
     classes = {}
-    if probe:
+    if probe and not batched:
         kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "sor_fine": V.VEMG_PROBE_SOR_FINE, "sor_all": V.VEMG_PROBE_SOR,
                  "residual": V.VEMG_PROBE_RESIDUAL}
         for name, kind in kinds.items():
@@ -275,8 +302,12 @@ def main():
     mesh = I.make_workload_mesh(args.workload)
     n = mesh.n
     vm = V.Mesh.from_inputs(mesh)
-    nb = min(args.steps + args.warmup, 8)
-    B = [torch.from_numpy(I.normal_loads(n, 2000 + 97 * rank + j)).cuda() for j in range(nb)]
+    kr = args.rhs or I.WORKLOADS[args.workload].get("nrhs", 1)
+    nb = min(args.steps + args.warmup, 8 if kr == 1 else 2)
+    if kr == 1:
+        B = [torch.from_numpy(I.normal_loads(n, 2000 + 97 * rank + j)).cuda() for j in range(nb)]
+    else:
+        B = [torch.from_numpy(I.normal_loads(n, 4000 + 997 * rank + 131 * j, k=kr)).cuda() for j in range(nb)]
 
     res = {}
     order = [args.precision] + [p for p in ("fp32", "fp64") if p != args.precision]
@@ -309,7 +340,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        r = time_oracle(mesh, B[0].cpu().numpy())
+        r = time_oracle(mesh, (B[0][0] if B[0].dim() == 2 else B[0]).cpu().numpy())
         cpu = {"value": 1.0 / r["solve_s"], "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": f"one full oracle solve of the {args.workload} workload ({r['iters']} iterations, "
                          f"{r['solve_s']:.1f} s; oracle setup {r['setup_s']:.1f} s not counted)"}

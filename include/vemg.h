@@ -156,6 +156,42 @@ int vemg_solve_host(vemg_hierarchy *h, const double *b_host, double *x_host, dou
 int vemg_solve_batch(vemg_hierarchy *h, int k, const double *B_dev, int64_t ldb, double *X_dev,
                      int64_t ldx, double rtol, int max_it, vemg_info *infos, void *stream);
 
+/* ---- continuous batching ----
+   An engine holds `slots` right-hand-side columns of one hierarchy (rounded up to a power of two,
+   at most 128). Requests are admitted into free slots between iterations and retired when done,
+   while the other slots keep iterating: each column has its own Krylov recurrence, tolerance and
+   iteration limit (the batched form of vemg_solve). Work is enqueued on the engine's stream, so
+   engines of different hierarchies on different streams run concurrently on the device. Each
+   engine owns its work memory (vemg_engine_bytes); one engine per hierarchy at a time. */
+typedef struct vemg_engine vemg_engine;
+
+#define VEMG_SLOT_FREE 0
+#define VEMG_SLOT_RUNNING 1
+#define VEMG_SLOT_DONE 2    /* converged, broken down or out of iterations: retire it */
+
+int vemg_engine_create(vemg_hierarchy *h, int slots, void *stream, vemg_engine **out);
+void vemg_engine_destroy(vemg_engine *e);
+
+/* Copy b (device, caller order) into a free slot, project it (Neumann) and start its iteration at
+   the next step. *slot receives the slot; VEMG_ENOMEM if no slot is free. Asynchronous. */
+int vemg_engine_admit(vemg_engine *e, const double *b_dev, double rtol, int max_it, int *slot);
+
+/* Enqueue `iters` iterations of every occupied slot and a copy of the slot states (asynchronous;
+   vemg_engine_wait completes it). */
+int vemg_engine_launch(vemg_engine *e, int iters);
+int vemg_engine_wait(vemg_engine *e);
+
+/* State of a slot after the last wait: VEMG_SLOT_FREE / RUNNING / DONE, and its info (iters,
+   status, recursive relres; true_relres = -1: not computed). */
+int vemg_engine_poll(const vemg_engine *e, int slot, vemg_info *info, int *state);
+
+/* Copy the slot's x (device, caller order, zero mean for Neumann, 0 on top nodes for Dirichlet-top)
+   and free the slot. Synchronises the engine's stream. */
+int vemg_engine_retire(vemg_engine *e, int slot, double *x_dev);
+
+int vemg_engine_slots(const vemg_engine *e, int *slots, int *free_slots);
+int vemg_engine_bytes(const vemg_engine *e, size_t *bytes);
+
 /* Device bytes held by a hierarchy (operators, transfer operators, work vectors). */
 int vemg_hierarchy_bytes(const vemg_hierarchy *h, size_t *bytes);
 

@@ -1,9 +1,14 @@
 // batch.cu -- many right-hand sides in one solve.
 //
 // K systems A x_c = b_c share one hierarchy. Vectors are interleaved (row-major n x K, K a power
-// of two): x[i*K + c]. In every sliced-ELL pass a group of KW = min(K, 32) lanes works on one row,
-// so each matrix entry is loaded once per warp and used for KW (or K) columns, and the gathers
-// x[j*K + c] of one entry are KW consecutive words. Each column keeps its own Krylov scalars
+// of two): x[i*K + c], in the natural (internal) ordering of each level. The operators are the
+// setup's natural-order CSR matrices: a group of KW = min(K, 32) lanes works on one row, the lanes
+// load KW consecutive entries of the row at once and pass them round by warp shuffles, so each
+// matrix entry is read once for all columns and the gathers x[j*K + c] are KW consecutive words.
+// Natural order keeps a row's neighbours close in memory, so the gathers stay in L2 even when the
+// K-column vectors are far larger than L2 (the colour-major order of the one-column solve does
+// not: each colour's pass would sweep the whole vector). Colour sweeps walk the level's list of
+// rows of each colour. Each column keeps its own Krylov scalars
 // (alpha, beta, norms, mean) and its own convergence test; a converged column is frozen (alpha = 0)
 // until every column has converged. The iteration runs as CUDA graphs with a WHILE node, like the
 // single right-hand-side solve (solve.cu); the V-cycles of the two branches run on two streams.
@@ -15,7 +20,6 @@
 
 namespace vemg {
 
-static constexpr int kBB = 304;        // blocks of the batched streaming / reduction kernels (2 per SM)
 static constexpr int kBT = 512;        // their threads
 static constexpr int kBU = 8;          // entries loaded per round trip in a batched row
 static constexpr int kMaxK = 128;      // widest batch
@@ -31,11 +35,33 @@ static thread_local int64_t *b_count = nullptr;
 // per-column scalar slots (sc[slot * K + c])
 enum {
     B_RZ = 0, B_PQ, B_ALPHA, B_BETA, B_MU, B_BN, B_RN, B_FLAG, B_ITERS, B_CONV, B_ZERO, B_TRUE, B_BMEAN, B_XMEAN,
-    B_COUNT
+    B_TOL, B_MAXIT, B_FRESH, B_COUNT
 };
 // global scalars after the per-column block (g[slot])
 enum { G_TOL = 0, G_MAXIT, G_CONT, G_ITERS, G_COUNT };
-enum { BC_SPMV = 0, BC_XR, BC_Z, BC_SUMB, BC_PREP, BC_SUMX, BC_TRUE, BC_COUNT };
+
+// one multigrid level as the batched cycle sees it
+struct BLevel {
+    int n = 0, ncolours = 0;
+    const int *rp = nullptr, *ci = nullptr, *colour = nullptr, *crow = nullptr;
+    const void *v = nullptr, *dinv = nullptr;
+    std::vector<int> cptr;
+    const int *prp = nullptr, *pci = nullptr, *trp = nullptr, *tci = nullptr;
+    const void *pv = nullptr, *tv = nullptr;
+};
+
+struct BChain {
+    int nlev = 0;
+    BLevel lv[kMaxLevels];
+    bool direct = false;
+    int nc = 0;
+    const double *G = nullptr;
+};
+
+struct CsrP {
+    const int *rp, *ci;
+    const void *v;
+};
 
 struct BatchGraphs {
     cudaGraph_t gpre = nullptr, gloop = nullptr, gpost = nullptr;
@@ -53,76 +79,128 @@ struct BatchWork {
     unsigned *ctr = nullptr;
     BatchGraphs *graphs = nullptr;
     Arena arena;
+    BChain *bsurf = nullptr, *bbar = nullptr;
+    CsrP Aout{};
+    const int *caller_of = nullptr;   // caller id of each unknown (internal order)
+    ~BatchWork() {
+        delete bsurf;
+        delete bbar;
+    }
 };
 
 static double *gsc(BatchWork *w) { return w->sc + B_COUNT * w->K; }
 
 // ------------------------------------------------------------------------------------------
-// batched sliced-ELL row operations
-
-struct SellP {
-    const int *row0, *nrow, *off, *width, *col;
-    const void *v;
-};
-
-static SellP sp(const Sell &S) { return SellP{S.row0, S.nrow, S.off, S.width, S.col, S.v}; }
+// batched CSR row operations (natural order)
 
 enum { BOP_SPMV = 0, BOP_SPMV_ADD = 1, BOP_SOR = 2, BOP_RES = 3 };
 
-// rows of the slices [s0, s1); KW lanes per row, columns c = lane % KW + j KW
+// Rows idx in [0, nrows): row = rows ? rows[idx] : r0 + idx, a group of KW lanes per row, columns
+// c = lane % KW + j KW. SOR skips the diagonal entry and, when sweeping from x = 0 (cur >= 0), every
+// entry whose column has colour >= cur (not yet visited: zero). RES keeps the diagonal: y = b - A x.
 template <int OP, class VT, class XT, class BT, class YT, class AT, int KW>
-__global__ void __launch_bounds__(32 * kSellWarps) k_bsell(int s0, int s1, SellP A, const VT *__restrict__ dg,
-                                                          const BT *__restrict__ b, const XT *x, YT *y, int K,
-                                                          int lim) {
-    constexpr int RW = 32 / KW;   // rows per warp
+__global__ void __launch_bounds__(32 * kSellWarps) k_bcsr(int nrows, const int *__restrict__ rows, int r0, CsrP A,
+                                                         const VT *__restrict__ dg, const BT *__restrict__ b,
+                                                         const XT *x, YT *y, int K, const int *__restrict__ colour,
+                                                         int cur) {
+    constexpr int RW = 32 / KW;
     int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    int s = s0 + w / KW;
-    if (s >= s1) return;
-    int ls = (w % KW) * RW + lane / KW;
-    if (ls >= A.nrow[s]) return;
-    int r = A.row0[s] + ls, o = A.off[s] + ls, wd = A.width[s];
+    if (w * RW >= nrows) return;   // warp-uniform
+    int idx = w * RW + lane / KW;
+    bool valid = idx < nrows;
+    int r = valid ? (rows ? rows[idx] : r0 + idx) : 0;
+    int lo = valid ? A.rp[r] : 0, wd = valid ? A.rp[r + 1] - lo : 0;
     const VT *v = (const VT *)A.v;
-    for (int c = lane % KW; c < K; c += KW) {
+    const int gl = lane % KW, gb = lane - gl;
+    const bool skip_all = OP == BOP_SOR && cur == 0;
+    int wmax = __reduce_max_sync(0xffffffffu, (unsigned)wd);
+    for (int c = gl; c < K; c += KW) {
         AT acc = 0;
-        if (!(OP == BOP_SOR && lim == 0)) {
-            for (int k0 = 0; k0 < wd; k0 += kBU) {
-                int cc[kBU];
-                VT a[kBU];
+        if (!skip_all) {
+            for (int k0 = 0; k0 < wmax; k0 += KW) {
+                int k = k0 + gl;
+                int cc = k < wd ? __ldg(A.ci + lo + k) : -1;
+                VT vv = k < wd ? __ldg(v + lo + k) : (VT)0;
+                if (OP == BOP_SOR && cc >= 0 && (cc == r || (cur > 0 && __ldg(colour + cc) >= cur))) cc = -1;
+                int nj = min(KW, wmax - k0);
 #pragma unroll
-                for (int u = 0; u < kBU; ++u) {
-                    int k = k0 + u;
-                    cc[u] = k < wd ? __ldg(A.col + o + 32 * k) : 0;
-                    a[u] = k < wd ? __ldg(v + o + 32 * k) : (VT)0;
+                for (int jj = 0; jj < KW; ++jj) {
+                    if (jj < nj) {
+                        int cj = __shfl_sync(0xffffffffu, cc, gb + jj);
+                        VT vj = __shfl_sync(0xffffffffu, vv, gb + jj);
+                        if (cj >= 0) acc += (AT)vj * (AT)x[(int64_t)cj * K + c];
+                    }
                 }
-#pragma unroll
-                for (int u = 0; u < kBU; ++u)
-                    if (k0 + u < wd && (lim < 0 || cc[u] < lim)) acc += (AT)a[u] * (AT)x[(int64_t)cc[u] * K + c];
             }
         }
+        if (!valid) continue;
         int64_t e = (int64_t)r * K + c;
         if (OP == BOP_SPMV) y[e] = (YT)acc;
         else if (OP == BOP_SPMV_ADD) y[e] = (YT)((AT)y[e] + acc);
         else if (OP == BOP_SOR) y[e] = (YT)(((AT)b[e] - acc) * (AT)dg[r]);
-        else y[e] = (YT)((AT)b[e] - ((AT)dg[r] * (AT)x[e] + acc));
+        else y[e] = (YT)((AT)b[e] - acc);
     }
 }
 
+// one lane per row and column group (K = 1, 2): entries loaded kBU at a time
+template <int OP, class VT, class XT, class BT, class YT, class AT, int KW>
+__global__ void __launch_bounds__(32 * kSellWarps) k_bcsr_narrow(int nrows, const int *__restrict__ rows, int r0,
+                                                                CsrP A, const VT *__restrict__ dg,
+                                                                const BT *__restrict__ b, const XT *x, YT *y, int K,
+                                                                const int *__restrict__ colour, int cur) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int idx = (int)(t / KW), c = (int)(t % KW);
+    if (idx >= nrows) return;
+    int r = rows ? rows[idx] : r0 + idx;
+    int lo = A.rp[r], hi = A.rp[r + 1];
+    const VT *v = (const VT *)A.v;
+    AT acc = 0;
+    if (!(OP == BOP_SOR && cur == 0)) {
+        for (int k0 = lo; k0 < hi; k0 += kBU) {
+            int cc[kBU];
+            VT a[kBU];
+#pragma unroll
+            for (int u = 0; u < kBU; ++u) {
+                int k = k0 + u;
+                cc[u] = k < hi ? __ldg(A.ci + k) : -1;
+                a[u] = k < hi ? __ldg(v + k) : (VT)0;
+                if (OP == BOP_SOR && cc[u] >= 0 && (cc[u] == r || (cur > 0 && __ldg(colour + cc[u]) >= cur))) cc[u] = -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kBU; ++u)
+                if (cc[u] >= 0) acc += (AT)a[u] * (AT)x[(int64_t)cc[u] * K + c];
+        }
+    }
+    int64_t e = (int64_t)r * K + c;
+    if (OP == BOP_SPMV) y[e] = (YT)acc;
+    else if (OP == BOP_SPMV_ADD) y[e] = (YT)((AT)y[e] + acc);
+    else if (OP == BOP_SOR) y[e] = (YT)(((AT)b[e] - acc) * (AT)dg[r]);
+    else y[e] = (YT)((AT)b[e] - acc);
+}
+
 template <int OP, class VT, class XT, class BT, class YT, class AT>
-static void bsell(const Sell &S, int s0, int s1, const VT *dg, const BT *b, const XT *x, YT *y, int K, int lim,
-                  cudaStream_t s) {
-    if (s1 <= s0) return;
+static void bcsr(CsrP A, int nrows, const int *rows, int r0, const VT *dg, const BT *b, const XT *x, YT *y, int K,
+                 const int *colour, int cur, cudaStream_t s) {
+    if (nrows <= 0) return;
     int KW = std::min(K, 32);
-    int64_t warps = (int64_t)(s1 - s0) * KW;
-    int grid = (int)((warps + kSellWarps - 1) / kSellWarps);
     dim3 blk(32 * kSellWarps);
-    SellP a = sp(S);
+    if (KW < 4) {
+        int64_t t = (int64_t)nrows * KW;
+        if (KW == 1)
+            k_bcsr_narrow<OP, VT, XT, BT, YT, AT, 1><<<grid_for(t, 32 * kSellWarps), blk, 0, s>>>(nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+        else
+            k_bcsr_narrow<OP, VT, XT, BT, YT, AT, 2><<<grid_for(t, 32 * kSellWarps), blk, 0, s>>>(nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+        BATCH_LAUNCHED();
+        return;
+    }
+    int RW = 32 / KW;
+    int64_t warps = (nrows + RW - 1) / RW;
+    int grid = (int)((warps + kSellWarps - 1) / kSellWarps);
     switch (KW) {
-        case 1: k_bsell<OP, VT, XT, BT, YT, AT, 1><<<grid, blk, 0, s>>>(s0, s1, a, dg, b, x, y, K, lim); break;
-        case 2: k_bsell<OP, VT, XT, BT, YT, AT, 2><<<grid, blk, 0, s>>>(s0, s1, a, dg, b, x, y, K, lim); break;
-        case 4: k_bsell<OP, VT, XT, BT, YT, AT, 4><<<grid, blk, 0, s>>>(s0, s1, a, dg, b, x, y, K, lim); break;
-        case 8: k_bsell<OP, VT, XT, BT, YT, AT, 8><<<grid, blk, 0, s>>>(s0, s1, a, dg, b, x, y, K, lim); break;
-        case 16: k_bsell<OP, VT, XT, BT, YT, AT, 16><<<grid, blk, 0, s>>>(s0, s1, a, dg, b, x, y, K, lim); break;
-        default: k_bsell<OP, VT, XT, BT, YT, AT, 32><<<grid, blk, 0, s>>>(s0, s1, a, dg, b, x, y, K, lim); break;
+        case 4: k_bcsr<OP, VT, XT, BT, YT, AT, 4><<<grid, blk, 0, s>>>(nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
+        case 8: k_bcsr<OP, VT, XT, BT, YT, AT, 8><<<grid, blk, 0, s>>>(nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
+        case 16: k_bcsr<OP, VT, XT, BT, YT, AT, 16><<<grid, blk, 0, s>>>(nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
+        default: k_bcsr<OP, VT, XT, BT, YT, AT, 32><<<grid, blk, 0, s>>>(nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
     }
     BATCH_LAUNCHED();
 }
@@ -139,17 +217,19 @@ __global__ void k_bdense(int n, const double *__restrict__ G, const BT *__restri
 }
 
 template <class XT, class BT>
-static void bsweep(const SLevel &L, const BT *b, XT *x, bool forward, bool from_zero, int K, cudaStream_t s) {
+static void bsweep(const BLevel &L, const BT *b, XT *x, bool forward, bool from_zero, int K, cudaStream_t s) {
+    CsrP A{L.rp, L.ci, L.v};
     for (int cc = 0; cc < L.ncolours; ++cc) {
         int c = forward ? cc : L.ncolours - 1 - cc;
-        int lim = from_zero ? L.crow[c] : -1;
-        bsell<BOP_SOR, XT, XT, BT, XT, XT>(L.A, L.cslice[c], L.cslice[c + 1], (const XT *)L.dinv, b, x, x, K, lim, s);
+        int nrows = L.cptr[c + 1] - L.cptr[c];
+        bcsr<BOP_SOR, XT, XT, BT, XT, XT>(A, nrows, L.crow + L.cptr[c], 0, (const XT *)L.dinv, b, x, x, K, L.colour,
+                                         from_zero ? c : -1, s);
     }
 }
 
 template <class XT, class BT>
-static void bvcycle(const SChain &C, BatchWork *W, int ch, int l, const BT *b, XT *x, cudaStream_t s) {
-    const SLevel &L = C.lv[l];
+static void bvcycle(const BChain &C, BatchWork *W, int ch, int l, const BT *b, XT *x, cudaStream_t s) {
+    const BLevel &L = C.lv[l];
     const int K = W->K;
     if (l == C.nlev - 1) {
         if (C.direct) {
@@ -164,22 +244,32 @@ static void bvcycle(const SChain &C, BatchWork *W, int ch, int l, const BT *b, X
     }
     XT *r = (XT *)W->lr[ch][l];
     XT *nb = (XT *)W->lb[ch][l + 1], *nx = (XT *)W->lx[ch][l + 1];
+    const BLevel &N = C.lv[l + 1];
     bsweep<XT, BT>(L, b, x, true, true, K, s);
-    bsell<BOP_RES, XT, XT, BT, XT, XT>(L.A, 0, L.A.nslices, (const XT *)L.diag, b, x, r, K, -1, s);
-    bsell<BOP_SPMV, XT, XT, XT, XT, XT>(L.PT, 0, L.PT.nslices, nullptr, (const XT *)nullptr, r, nb, K, -1, s);
+    bcsr<BOP_RES, XT, XT, BT, XT, XT>(CsrP{L.rp, L.ci, L.v}, L.n, nullptr, 0, (const XT *)nullptr, b, x, r, K,
+                                      nullptr, -1, s);
+    bcsr<BOP_SPMV, XT, XT, XT, XT, XT>(CsrP{L.trp, L.tci, L.tv}, N.n, nullptr, 0, (const XT *)nullptr,
+                                       (const XT *)nullptr, r, nb, K, nullptr, -1, s);
     bvcycle<XT, XT>(C, W, ch, l + 1, (const XT *)nb, nx, s);
-    bsell<BOP_SPMV_ADD, XT, XT, XT, XT, XT>(L.P, 0, L.P.nslices, nullptr, (const XT *)nullptr, nx, x, K, -1, s);
+    bcsr<BOP_SPMV_ADD, XT, XT, XT, XT, XT>(CsrP{L.prp, L.pci, L.pv}, L.n, nullptr, 0, (const XT *)nullptr,
+                                           (const XT *)nullptr, nx, x, K, nullptr, -1, s);
     bsweep<XT, BT>(L, b, x, false, false, K, s);
 }
 
 // ------------------------------------------------------------------------------------------
-// per-column deterministic reductions: each thread accumulates for column c = tid % K (K divides
-// the block size); blocks write per-column partials; the last block adds them in block order.
+// per-column deterministic reductions in two stages. Stage 1 (streaming kernels): each block
+// covers kBT * kBE consecutive elements of the n x K block; thread t always holds column
+// t % K (K divides kBT), loads its kBE elements first, and the block writes one partial per
+// column and sum. Stage 2 (k_bstage2): one block per column adds the block partials in fixed
+// order and applies the scalar step of that column; the last column block sets the globals.
+
+static constexpr int kBE = 8;   // elements per thread in stage 1
+
+static int stage1_blocks(int64_t N) { return (int)((N + (int64_t)kBT * kBE - 1) / ((int64_t)kBT * kBE)); }
 
 template <int NS>
-__device__ bool bfinish(double (&acc)[NS], int K, double *part, unsigned *counter) {
+__device__ void bblock_partials(double (&acc)[NS], int K, double *part) {
     __shared__ double sh[kBT];
-    __shared__ bool last;
     const int t = threadIdx.x;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
@@ -188,241 +278,173 @@ __device__ bool bfinish(double (&acc)[NS], int K, double *part, unsigned *counte
         if (t < K) {
             double v = 0.0;
             for (int j = t; j < kBT; j += K) v += sh[j];
-            part[((int64_t)s * kBB + blockIdx.x) * K + t] = v;
+            part[((int64_t)blockIdx.x * NS + s) * K + t] = v;
         }
         __syncthreads();
     }
-    __threadfence();
-    __syncthreads();
-    if (t == 0) last = atomicAdd(counter, 1u) == (unsigned)(kBB - 1);
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    return true;
 }
 
-// in the last block: total of sum slot s for column c
-__device__ double btotal(const double *part, int s, int c, int K) {
-    double v = 0.0;
-#pragma unroll 8
-    for (int k = 0; k < kBB; ++k) v += __ldcg(part + ((int64_t)s * kBB + k) * K + c);
-    return v;
-}
+// stage-1 sums: s0 = sum a*b (or sum a when b is null), s1 = sum c*d (or sum c), ...
+struct BSums {
+    const double *a[5];
+    const double *b[5];
+    int ns;
+};
 
-// mean of each column; stored in sc[slot * K + c]
-__global__ void __launch_bounds__(kBT) k_bmean(int n, int K, const double *__restrict__ a, double inv_n, int slot,
-                                              double *sc, double *part, unsigned *ctr) {
-    double acc[1] = {0.0};
-    int64_t N = (int64_t)n * K;
-    for (int64_t e = blockIdx.x * (int64_t)kBT + threadIdx.x; e < N; e += (int64_t)kBB * kBT) acc[0] += a[e];
-    if (!bfinish<1>(acc, K, part, ctr)) return;
-    for (int c = threadIdx.x; c < K; c += kBT) sc[slot * K + c] = btotal(part, 0, c, K) * inv_n;
-    __syncthreads();
-    if (threadIdx.x == 0) *ctr = 0u;
-}
-
-// b -= mean (Neumann), r = b, x = p = 0; per-column ||b||, zero columns are converged at once
-__global__ void __launch_bounds__(kBT) k_bprepare(int n, int K, int neumann, double *__restrict__ b,
-                                                 double *__restrict__ r, double *__restrict__ x,
-                                                 double *__restrict__ p, double *sc, double *part, unsigned *ctr) {
-    double acc[1] = {0.0};
-    int64_t N = (int64_t)n * K;
-    for (int64_t e = blockIdx.x * (int64_t)kBT + threadIdx.x; e < N; e += (int64_t)kBB * kBT) {
-        int c = (int)(e & (K - 1));
-        double bi = b[e] - (neumann ? sc[B_BMEAN * K + c] : 0.0);
-        b[e] = bi;
-        r[e] = bi;
-        x[e] = 0.0;
-        p[e] = 0.0;
-        acc[0] += bi * bi;
-    }
-    if (!bfinish<1>(acc, K, part, ctr)) return;
-    for (int c = threadIdx.x; c < K; c += kBT) {
-        double bn = sqrt(btotal(part, 0, c, K));
-        sc[B_BN * K + c] = bn;
-        if (bn == 0.0) {
-            sc[B_ZERO * K + c] = 1.0;
-            sc[B_CONV * K + c] = 1.0;
+template <int NS>
+__global__ void __launch_bounds__(kBT) k_bsums(int64_t N, int K, BSums d, double *part) {
+    double acc[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) acc[s] = 0.0;
+    int64_t base = (int64_t)blockIdx.x * kBT * kBE + threadIdx.x;
+    double va[NS][kBE], vb[NS][kBE];
+#pragma unroll
+    for (int j = 0; j < kBE; ++j) {
+        int64_t e = base + (int64_t)j * kBT;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            va[s][j] = e < N ? d.a[s][e] : 0.0;
+            vb[s][j] = (e < N && d.b[s]) ? d.b[s][e] : 1.0;
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) *ctr = 0u;
+#pragma unroll
+    for (int j = 0; j < kBE; ++j)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) acc[s] += va[s][j] * vb[s][j];
+    bblock_partials<NS>(acc, K, part);
 }
 
-// Q = A P over all slices of the FP64 outer operator with per-column (p, q); alpha per column
-template <int KW>
-__global__ void __launch_bounds__(kBT) k_bspmv_pq(int nsl, SellP A, int K, const double *__restrict__ p,
-                                                 double *__restrict__ q, double *sc, double *part, unsigned *ctr) {
-    constexpr int RW = 32 / KW;
-    constexpr int JK_MAX = kMaxK / 32 > 0 ? kMaxK / 32 : 1;
-    const int lane = threadIdx.x & 31;
-    const double *v = (const double *)A.v;
-    double accj[JK_MAX];
+enum { ST_MEAN_B = 0, ST_BN, ST_ALPHA, ST_RN, ST_BETA, ST_MEAN_X, ST_TRUE };
+
+// stage 2: one block per column
+__global__ void __launch_bounds__(256) k_bstage2(int op, int nblk, int ns, int K, const double *__restrict__ part,
+                                                double *sc, double inv_n, int neumann, int flexible, int first,
+                                                unsigned *ctr, int *active, cudaGraphConditionalHandle handle,
+                                                int use_cond) {
+    __shared__ double red[256 / 32];
+    __shared__ double tot[5];
+    const int c = blockIdx.x, t = threadIdx.x;
+    for (int s = 0; s < ns; ++s) {
+        double v = 0.0;
+        for (int k = t; k < nblk; k += 256) v += part[((int64_t)k * ns + s) * K + c];
 #pragma unroll
-    for (int j = 0; j < JK_MAX; ++j) accj[j] = 0.0;
-    int nw_total = kBB * (kBT / 32);
-    for (int w = blockIdx.x * (kBT / 32) + (threadIdx.x >> 5); w < nsl * KW; w += nw_total) {
-        int s = w / KW, ls = (w % KW) * RW + lane / KW;
-        if (ls >= A.nrow[s]) continue;
-        int r = A.row0[s] + ls, o = A.off[s] + ls, wd = A.width[s];
-        int j = 0;
-        for (int c = lane % KW; c < K; c += KW, ++j) {
-            double acc = 0.0;
-            for (int k0 = 0; k0 < wd; k0 += kBU) {
-                int cc[kBU];
-                double a[kBU];
-#pragma unroll
-                for (int u = 0; u < kBU; ++u) {
-                    int k = k0 + u;
-                    cc[u] = k < wd ? __ldg(A.col + o + 32 * k) : 0;
-                    a[u] = k < wd ? __ldg(v + o + 32 * k) : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < kBU; ++u)
-                    if (k0 + u < wd) acc += a[u] * p[(int64_t)cc[u] * K + c];
-            }
-            int64_t e = (int64_t)r * K + c;
-            q[e] = acc;
-            accj[j] += p[e] * acc;
-        }
-    }
-    // per-thread accumulators belong to columns lane % KW + j KW; fold them into the layout
-    // bfinish expects (column = tid % K) through shared memory
-    __shared__ double sh[kBT];
-    double tot_thread = 0.0;
-    if (K <= 32) {
-        // tid % K == lane % KW here (KW == K, 32 % K == 0)
-        tot_thread = accj[0];
-        double acc1[1] = {tot_thread};
-        if (!bfinish<1>(acc1, K, part, ctr)) return;
-    } else {
-        // K > 32: each lane holds columns lane + 32 j; write them to a (block, column) scratch row
-        double colsum[1] = {0.0};
-        (void)colsum;
-        for (int j = 0; j < K / 32; ++j) {
-            sh[threadIdx.x] = accj[j];
-            __syncthreads();
-            // column c = lane + 32 j: sum over the block's warps
-            if (threadIdx.x < 32) {
-                double vv = 0.0;
-                for (int ww = 0; ww < kBT / 32; ++ww) vv += sh[ww * 32 + threadIdx.x];
-                part[(int64_t)blockIdx.x * K + threadIdx.x + 32 * j] = vv;
-            }
-            __syncthreads();
-        }
-        __shared__ bool last;
-        __threadfence();
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((t & 31) == 0) red[t >> 5] = v;
         __syncthreads();
-        if (threadIdx.x == 0) last = atomicAdd(ctr, 1u) == (unsigned)(kBB - 1);
+        if (t == 0) {
+            double w = 0.0;
+            for (int i = 0; i < 256 / 32; ++i) w += red[i];
+            tot[s] = w;
+        }
         __syncthreads();
-        if (!last) return;
-        __threadfence();
     }
-    for (int c = threadIdx.x; c < K; c += kBT) {
-        double pq = btotal(part, 0, c, K);
-        sc[B_PQ * K + c] = pq;
-        if (sc[B_CONV * K + c] != 0.0 || sc[B_FLAG * K + c] != 0.0) sc[B_ALPHA * K + c] = 0.0;
-        else if (!(pq > 0.0)) {
-            sc[B_FLAG * K + c] = 1.0;
-            sc[B_ALPHA * K + c] = 0.0;
-        } else sc[B_ALPHA * K + c] = sc[B_RZ * K + c] / pq;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *ctr = 0u;
-}
-
-// X += alpha P, R -= alpha Q per column, per-column ||r||, convergence, WHILE condition
-__global__ void __launch_bounds__(kBT) k_bupdate_xr(int n, int K, const double *__restrict__ p,
-                                                   const double *__restrict__ q, double *__restrict__ x,
-                                                   double *__restrict__ r, double *sc, double *part, unsigned *ctr,
-                                                   cudaGraphConditionalHandle handle, int use_cond) {
-    double acc[1] = {0.0};
-    int64_t N = (int64_t)n * K;
-    for (int64_t e = blockIdx.x * (int64_t)kBT + threadIdx.x; e < N; e += (int64_t)kBB * kBT) {
-        int c = (int)(e & (K - 1));
-        double a = sc[B_ALPHA * K + c];
-        x[e] += a * p[e];
-        double ri = r[e] - a * q[e];
-        r[e] = ri;
-        acc[0] += ri * ri;
-    }
-    if (!bfinish<1>(acc, K, part, ctr)) return;
-    __shared__ int active;
-    if (threadIdx.x == 0) active = 0;
-    __syncthreads();
     double *g = sc + B_COUNT * K;
-    for (int c = threadIdx.x; c < K; c += kBT) {
-        double rn = sqrt(btotal(part, 0, c, K));
-        if (sc[B_CONV * K + c] == 0.0 && sc[B_FLAG * K + c] == 0.0) {
-            sc[B_RN * K + c] = rn;
-            sc[B_ITERS * K + c] += 1.0;
-            if (!(rn == rn)) sc[B_FLAG * K + c] = 1.0;
-            else if (rn <= g[G_TOL] * sc[B_BN * K + c]) sc[B_CONV * K + c] = 1.0;
-            if (sc[B_CONV * K + c] == 0.0 && sc[B_FLAG * K + c] == 0.0 && sc[B_ITERS * K + c] < g[G_MAXIT])
-                atomicOr(&active, 1);
+    if (t == 0) {
+        // converged, broken down, or out of iterations: frozen while other columns continue
+        bool frozen = sc[B_CONV * K + c] != 0.0 || sc[B_FLAG * K + c] != 0.0 ||
+                      sc[B_ITERS * K + c] >= sc[B_MAXIT * K + c];
+        switch (op) {
+            case ST_MEAN_B: sc[B_BMEAN * K + c] = tot[0] * inv_n; break;
+            case ST_MEAN_X: sc[B_XMEAN * K + c] = tot[0] * inv_n; break;
+            case ST_TRUE: sc[B_TRUE * K + c] = sqrt(tot[0]); break;
+            case ST_BN: {
+                double bn = sqrt(tot[0]);
+                sc[B_BN * K + c] = bn;
+                if (bn == 0.0) {
+                    sc[B_ZERO * K + c] = 1.0;
+                    sc[B_CONV * K + c] = 1.0;
+                } else if (sc[B_MAXIT * K + c] > 0.0) {
+                    atomicOr(active, 1);
+                }
+                __threadfence();
+                if (atomicAdd(ctr, 1u) == (unsigned)(K - 1)) {
+                    g[G_CONT] = atomicAdd(active, 0) ? 1.0 : 0.0;
+                    *active = 0;
+                    *ctr = 0u;
+                }
+                break;
+            }
+            case ST_ALPHA: {
+                double pq = tot[0];
+                sc[B_PQ * K + c] = pq;
+                if (frozen) sc[B_ALPHA * K + c] = 0.0;
+                else if (!(pq > 0.0)) {
+                    sc[B_FLAG * K + c] = 1.0;
+                    sc[B_ALPHA * K + c] = 0.0;
+                } else sc[B_ALPHA * K + c] = sc[B_RZ * K + c] / pq;
+                break;
+            }
+            case ST_RN: {
+                double rn = sqrt(tot[0]);
+                if (!frozen) {
+                    sc[B_RN * K + c] = rn;
+                    sc[B_ITERS * K + c] += 1.0;
+                    if (!(rn == rn)) sc[B_FLAG * K + c] = 1.0;
+                    else if (rn <= sc[B_TOL * K + c] * sc[B_BN * K + c]) sc[B_CONV * K + c] = 1.0;
+                    if (sc[B_CONV * K + c] == 0.0 && sc[B_FLAG * K + c] == 0.0 &&
+                        sc[B_ITERS * K + c] < sc[B_MAXIT * K + c])
+                        atomicOr(active, 1);
+                }
+                __threadfence();
+                if (atomicAdd(ctr, 1u) == (unsigned)(K - 1)) {
+                    // last column: every other column's flag is visible
+                    int act = atomicAdd(active, 0);
+                    g[G_ITERS] += 1.0;
+                    g[G_CONT] = act ? 1.0 : 0.0;
+                    if (use_cond) cudaGraphSetConditional(handle, act ? 1u : 0u);
+                    *active = 0;
+                    *ctr = 0u;
+                }
+                break;
+            }
+            case ST_BETA: {
+                double mu = neumann ? tot[0] * inv_n : 0.0;
+                double rz = tot[1] - mu * tot[2];
+                double beta = 0.0;
+                const bool fresh = sc[B_FRESH * K + c] != 0.0;
+                sc[B_FRESH * K + c] = 0.0;
+                if (!fresh && !frozen) {
+                    if (flexible) beta = -(tot[3] - mu * tot[4]) / sc[B_PQ * K + c];
+                    else beta = rz / sc[B_RZ * K + c];
+                    if (!(rz == rz) || !(beta == beta)) sc[B_FLAG * K + c] = 1.0;
+                }
+                sc[B_MU * K + c] = mu;
+                sc[B_BETA * K + c] = frozen ? 0.0 : beta;
+                sc[B_RZ * K + c] = rz;
+                break;
+            }
         }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        g[G_ITERS] += 1.0;
-        g[G_CONT] = active ? 1.0 : 0.0;
-        if (use_cond) cudaGraphSetConditional(handle, active ? 1u : 0u);
-        *ctr = 0u;
     }
 }
 
-// Z from the two branches and per-column t0 = sum z, t1 = (r, z), t2 = sum r, t3 = (z, q),
-// t4 = sum q; then per column mu, rz = (r, z - mu), beta (0 on the first direction and on frozen
-// columns; CG: rz'/rz; FCG: -(z - mu, q) / (p, q))
+// b -= mean (Neumann), r = b, x = p = 0 (streaming, no reduction)
+__global__ void k_bprepare(int64_t N, int K, int neumann, double *__restrict__ b, double *__restrict__ r,
+                           double *__restrict__ x, double *__restrict__ p, const double *__restrict__ sc) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    double bi = b[e] - (neumann ? sc[B_BMEAN * K + (int)(e & (K - 1))] : 0.0);
+    b[e] = bi;
+    r[e] = bi;
+    x[e] = 0.0;
+    p[e] = 0.0;
+}
+
+// X += alpha P, R -= alpha Q per column
+__global__ void k_bupdate_xr(int64_t N, int K, const double *__restrict__ p, const double *__restrict__ q,
+                             double *__restrict__ x, double *__restrict__ r, const double *__restrict__ sc) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    double a = sc[B_ALPHA * K + (int)(e & (K - 1))];
+    x[e] += a * p[e];
+    r[e] -= a * q[e];
+}
+
+// z += x (assign: z = x)
 template <class XT>
-__global__ void __launch_bounds__(kBT) k_bcombine(int nu, int K, int mtop, SellP E, const XT *__restrict__ ys,
-                                                 const XT *__restrict__ xb, double *__restrict__ z,
-                                                 const double *__restrict__ r, const double *__restrict__ q,
-                                                 int neumann, int flexible, int first, double inv_n, double *sc,
-                                                 double *part, unsigned *ctr) {
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    const bool dq = flexible && !first;
-    const double *ev = (const double *)E.v;
-    int64_t N = (int64_t)nu * K;
-    for (int64_t e = blockIdx.x * (int64_t)kBT + threadIdx.x; e < N; e += (int64_t)kBB * kBT) {
-        int i = (int)(e >> (__ffs(K) - 1)), c = (int)(e & (K - 1));
-        double zi;
-        if (i < mtop) zi = (double)ys[e];
-        else if (mtop > 0) {
-            int qq = i - mtop, sl = qq >> 5, ln = qq & 31;
-            int o = E.off[sl] + ln, w = E.width[sl];
-            zi = (double)xb[(int64_t)qq * K + c];
-            for (int k = 0; k < w; ++k) zi += ev[o + 32 * k] * (double)ys[(int64_t)E.col[o + 32 * k] * K + c];
-        } else zi = (double)xb[e];
-        z[e] = zi;
-        double ri = r[e];
-        acc[0] += zi;
-        acc[1] += ri * zi;
-        acc[2] += ri;
-        if (dq) {
-            double qi = q[e];
-            acc[3] += zi * qi;
-            acc[4] += qi;
-        }
-    }
-    if (!bfinish<5>(acc, K, part, ctr)) return;
-    for (int c = threadIdx.x; c < K; c += kBT) {
-        double t0 = btotal(part, 0, c, K), t1 = btotal(part, 1, c, K), t2 = btotal(part, 2, c, K);
-        double mu = neumann ? t0 * inv_n : 0.0;
-        double rz = t1 - mu * t2;
-        double beta = 0.0;
-        bool frozen = sc[B_CONV * K + c] != 0.0 || sc[B_FLAG * K + c] != 0.0;
-        if (!first && !frozen) {
-            if (flexible) beta = -(btotal(part, 3, c, K) - mu * btotal(part, 4, c, K)) / sc[B_PQ * K + c];
-            else beta = rz / sc[B_RZ * K + c];
-            if (!(rz == rz) || !(beta == beta)) sc[B_FLAG * K + c] = 1.0;
-        }
-        sc[B_MU * K + c] = mu;
-        sc[B_BETA * K + c] = frozen ? 0.0 : beta;
-        sc[B_RZ * K + c] = rz;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *ctr = 0u;
+__global__ void k_badd(int64_t N, const XT *__restrict__ x, double *__restrict__ z, int assign = 0) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    z[e] = assign ? (double)x[e] : z[e] + (double)x[e];
 }
 
 // P = (Z - mu) + beta P per column
@@ -439,64 +461,17 @@ __global__ void k_bsub_mean(int64_t N, int K, double *__restrict__ x, const doub
     if (e < N) x[e] -= sc[slot * K + (int)(e & (K - 1))];
 }
 
-// per-column ||b - A x|| (true residual), one thread per (row, column) group of the outer operator
-template <int KW>
-__global__ void __launch_bounds__(kBT) k_btrue(int nsl, SellP A, int K, const double *__restrict__ x,
-                                              const double *__restrict__ b, double *sc, double *part, unsigned *ctr) {
-    // reuses the layout of k_bspmv_pq: columns lane % KW + j KW
-    constexpr int RW = 32 / KW;
-    constexpr int JK_MAX = kMaxK / 32 > 0 ? kMaxK / 32 : 1;
-    const int lane = threadIdx.x & 31;
-    const double *v = (const double *)A.v;
-    double accj[JK_MAX];
-#pragma unroll
-    for (int j = 0; j < JK_MAX; ++j) accj[j] = 0.0;
-    for (int w = blockIdx.x * (kBT / 32) + (threadIdx.x >> 5); w < nsl * KW; w += kBB * (kBT / 32)) {
-        int s = w / KW, ls = (w % KW) * RW + lane / KW;
-        if (ls >= A.nrow[s]) continue;
-        int r = A.row0[s] + ls, o = A.off[s] + ls, wd = A.width[s];
-        int j = 0;
-        for (int c = lane % KW; c < K; c += KW, ++j) {
-            double acc = 0.0;
-            for (int k = 0; k < wd; ++k) acc += __ldg(v + o + 32 * k) * x[(int64_t)__ldg(A.col + o + 32 * k) * K + c];
-            double d = b[(int64_t)r * K + c] - acc;
-            accj[j] += d * d;
-        }
-    }
-    __shared__ double sh[kBT];
-    if (K <= 32) {
-        double acc1[1] = {accj[0]};
-        if (!bfinish<1>(acc1, K, part, ctr)) return;
-    } else {
-        for (int j = 0; j < K / 32; ++j) {
-            sh[threadIdx.x] = accj[j];
-            __syncthreads();
-            if (threadIdx.x < 32) {
-                double vv = 0.0;
-                for (int ww = 0; ww < kBT / 32; ++ww) vv += sh[ww * 32 + threadIdx.x];
-                part[(int64_t)blockIdx.x * K + threadIdx.x + 32 * j] = vv;
-            }
-            __syncthreads();
-        }
-        __shared__ bool last;
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) last = atomicAdd(ctr, 1u) == (unsigned)(kBB - 1);
-        __syncthreads();
-        if (!last) return;
-        __threadfence();
-    }
-    for (int c = threadIdx.x; c < K; c += kBT) sc[B_TRUE * K + c] = sqrt(btotal(part, 0, c, K));
-    __syncthreads();
-    if (threadIdx.x == 0) *ctr = 0u;
-}
 
 __global__ void k_binit(double *sc, int K, double tol, int maxit) {
     for (int i = 0; i < B_COUNT * K + G_COUNT; ++i) sc[i] = 0.0;
+    for (int c = 0; c < K; ++c) {
+        sc[B_TOL * K + c] = tol;
+        sc[B_MAXIT * K + c] = (double)maxit;
+        sc[B_FRESH * K + c] = 1.0;
+    }
     double *g = sc + B_COUNT * K;
     g[G_TOL] = tol;
     g[G_MAXIT] = (double)maxit;
-    g[G_CONT] = maxit > 0 ? 1.0 : 0.0;
 }
 
 // gather k caller-order columns (column c at B[c * ldb]) into the interleaved solve-order block
@@ -527,89 +502,103 @@ __global__ void k_bcond_init(const double *g, cudaGraphConditionalHandle handle)
 // the batched iteration
 
 template <class XT>
-static void bprecond(vemg_hierarchy *h, BatchWork *W, int first, cudaStream_t s) {
+static void bprecond(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
     const int K = W->K;
-    const bool neu = h->bc == VEMG_NEUMANN, flex = h->precision != VEMG_PREC_FP64;
+    const bool neu = h->bc == VEMG_NEUMANN;
     const int mt = neu ? h->mtop : 0;
-    const SChain &B = h->sbar;
-    const XT *ys = nullptr;
+    XT *xb = (XT *)W->lx[1][0];
     if (neu) {
-        const SChain &S = h->ssurf;
+        XT *b0 = (XT *)W->lb[0][0], *x0 = (XT *)W->lx[0][0];
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_fork, s));
         VEMG_CHECK_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-        XT *b0 = (XT *)W->lb[0][0], *x0 = (XT *)W->lx[0][0];
-        bsell<BOP_SPMV, double, double, double, XT, double>(h->ETs, 0, h->ETs.nslices, nullptr, (const double *)nullptr,
-                                                            W->R, b0, K, -1, h->side);
-        bvcycle<XT, XT>(S, W, 0, 0, (const XT *)b0, x0, h->side);
+        // surface branch: r_c = E~^T r in FP64, one V-cycle on E~^T A E~
+        bcsr<BOP_SPMV, double, double, double, XT, double>(CsrP{h->ET.rp, h->ET.ci, h->ET.v}, h->mtop, nullptr, 0,
+                                                           (const double *)nullptr, (const double *)nullptr, W->R,
+                                                           b0, K, nullptr, -1, h->side);
+        bvcycle<XT, XT>(*W->bsurf, W, 0, 0, (const XT *)b0, x0, h->side);
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_join, h->side));
-        ys = x0;
+        bvcycle<XT, double>(*W->bbar, W, 1, 0, W->R + (int64_t)mt * K, xb, s);
+        VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+        // z = E~ y_s + [0; x_bar]
+        bcsr<BOP_SPMV, double, XT, double, double, double>(CsrP{h->E.rp, h->E.ci, h->E.v}, h->n, nullptr, 0,
+                                                           (const double *)nullptr, (const double *)nullptr, x0, W->Z,
+                                                           K, nullptr, -1, s);
+        int64_t nbk = (int64_t)(h->n - mt) * K;
+        k_badd<XT><<<grid_for(nbk, 256), 256, 0, s>>>(nbk, xb, W->Z + (int64_t)mt * K);
+        BATCH_LAUNCHED();
+    } else {
+        bvcycle<XT, double>(*W->bbar, W, 1, 0, W->R, xb, s);
+        int64_t N = (int64_t)h->nu * K;
+        k_badd<XT><<<grid_for(N, 256), 256, 0, s>>>(N, xb, W->Z, 1);
+        BATCH_LAUNCHED();
     }
-    XT *xb = (XT *)W->lx[1][0];
-    bvcycle<XT, double>(B, W, 1, 0, W->R + (int64_t)mt * K, xb, s);
-    if (neu) VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
-    k_bcombine<XT><<<kBB, kBT, 0, s>>>(h->nu, K, mt, sp(h->Enon), ys, xb, W->Z, W->R, W->Q, neu, flex, first,
-                                       1.0 / (double)h->nu, W->sc, W->part + (int64_t)5 * kBB * K * BC_Z,
-                                       W->ctr + BC_Z);
+}
+
+static void bsums(BatchWork *W, int64_t N, const BSums &d, cudaStream_t s) {
+    int nblk = stage1_blocks(N);
+    switch (d.ns) {
+        case 1: k_bsums<1><<<nblk, kBT, 0, s>>>(N, W->K, d, W->part); break;
+        case 3: k_bsums<3><<<nblk, kBT, 0, s>>>(N, W->K, d, W->part); break;
+        default: k_bsums<5><<<nblk, kBT, 0, s>>>(N, W->K, d, W->part); break;
+    }
+    BATCH_LAUNCHED();
+}
+
+static void bstage2(vemg_hierarchy *h, BatchWork *W, int op, int ns, int64_t N, int first, cudaStream_t s,
+                    cudaGraphConditionalHandle hd = 0, int use_cond = 0) {
+    k_bstage2<<<W->K, 256, 0, s>>>(op, stage1_blocks(N), ns, W->K, W->part, W->sc, 1.0 / (double)h->nu,
+                                   h->bc == VEMG_NEUMANN, h->precision != VEMG_PREC_FP64, first, W->ctr,
+                                   (int *)(W->ctr + 1), hd, use_cond);
     BATCH_LAUNCHED();
 }
 
 static void bprecond_any(vemg_hierarchy *h, BatchWork *W, int first, cudaStream_t s) {
-    if (h->precision == VEMG_PREC_FP32) bprecond<float>(h, W, first, s);
-    else bprecond<double>(h, W, first, s);
+    if (h->precision == VEMG_PREC_FP32) bprecond<float>(h, W, s);
+    else bprecond<double>(h, W, s);
+    // t0 = sum z, t1 = (r, z), t2 = sum r [, t3 = (z, q), t4 = sum q]
+    int64_t N = (int64_t)h->nu * W->K;
+    bool flex = h->precision != VEMG_PREC_FP64;
+    (void)first;
+    BSums d{{W->Z, W->R, W->R, W->Z, W->Q}, {nullptr, W->Z, nullptr, W->Q, nullptr}, flex ? 5 : 3};
+    bsums(W, N, d, s);
+    bstage2(h, W, ST_BETA, d.ns, N, first, s);
 }
 
-static double *bpart(BatchWork *W, int c) { return W->part + (int64_t)5 * kBB * W->K * c; }
-
-static void bspmv_pq(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
-    const int K = W->K, KW = std::min(K, 32);
-    SellP A = sp(h->Aop);
-    int nsl = h->Aop.nslices;
-    switch (KW) {
-        case 1: k_bspmv_pq<1><<<kBB, kBT, 0, s>>>(nsl, A, K, W->P, W->Q, W->sc, bpart(W, BC_SPMV), W->ctr + BC_SPMV); break;
-        case 2: k_bspmv_pq<2><<<kBB, kBT, 0, s>>>(nsl, A, K, W->P, W->Q, W->sc, bpart(W, BC_SPMV), W->ctr + BC_SPMV); break;
-        case 4: k_bspmv_pq<4><<<kBB, kBT, 0, s>>>(nsl, A, K, W->P, W->Q, W->sc, bpart(W, BC_SPMV), W->ctr + BC_SPMV); break;
-        case 8: k_bspmv_pq<8><<<kBB, kBT, 0, s>>>(nsl, A, K, W->P, W->Q, W->sc, bpart(W, BC_SPMV), W->ctr + BC_SPMV); break;
-        case 16: k_bspmv_pq<16><<<kBB, kBT, 0, s>>>(nsl, A, K, W->P, W->Q, W->sc, bpart(W, BC_SPMV), W->ctr + BC_SPMV); break;
-        default: k_bspmv_pq<32><<<kBB, kBT, 0, s>>>(nsl, A, K, W->P, W->Q, W->sc, bpart(W, BC_SPMV), W->ctr + BC_SPMV); break;
-    }
-    BATCH_LAUNCHED();
-}
-
-static void btrue(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
-    const int K = W->K, KW = std::min(K, 32);
-    SellP A = sp(h->Aop);
-    int nsl = h->Aop.nslices;
-    switch (KW) {
-        case 1: k_btrue<1><<<kBB, kBT, 0, s>>>(nsl, A, K, W->X, W->B, W->sc, bpart(W, BC_TRUE), W->ctr + BC_TRUE); break;
-        case 2: k_btrue<2><<<kBB, kBT, 0, s>>>(nsl, A, K, W->X, W->B, W->sc, bpart(W, BC_TRUE), W->ctr + BC_TRUE); break;
-        case 4: k_btrue<4><<<kBB, kBT, 0, s>>>(nsl, A, K, W->X, W->B, W->sc, bpart(W, BC_TRUE), W->ctr + BC_TRUE); break;
-        case 8: k_btrue<8><<<kBB, kBT, 0, s>>>(nsl, A, K, W->X, W->B, W->sc, bpart(W, BC_TRUE), W->ctr + BC_TRUE); break;
-        case 16: k_btrue<16><<<kBB, kBT, 0, s>>>(nsl, A, K, W->X, W->B, W->sc, bpart(W, BC_TRUE), W->ctr + BC_TRUE); break;
-        default: k_btrue<32><<<kBB, kBT, 0, s>>>(nsl, A, K, W->X, W->B, W->sc, bpart(W, BC_TRUE), W->ctr + BC_TRUE); break;
-    }
-    BATCH_LAUNCHED();
-}
-
+// b -= mean (Neumann), r = b, x = p = 0, ||b|| per column; the iterations themselves start in the
+// loop body, where every column enters as fresh (first direction p = z - mu)
 static void bphase_pre(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
     const int K = W->K, nu = h->nu;
+    const int64_t N = (int64_t)nu * K;
     const bool neu = h->bc == VEMG_NEUMANN;
     if (neu) {
-        k_bmean<<<kBB, kBT, 0, s>>>(nu, K, W->B, 1.0 / (double)nu, B_BMEAN, W->sc, bpart(W, BC_SUMB), W->ctr + BC_SUMB);
-        BATCH_LAUNCHED();
+        BSums d{{W->B}, {nullptr}, 1};
+        bsums(W, N, d, s);
+        bstage2(h, W, ST_MEAN_B, 1, N, 0, s);
     }
-    k_bprepare<<<kBB, kBT, 0, s>>>(nu, K, neu, W->B, W->R, W->X, W->P, W->sc, bpart(W, BC_PREP), W->ctr + BC_PREP);
+    k_bprepare<<<grid_for(N, 256), 256, 0, s>>>(N, K, neu, W->B, W->R, W->X, W->P, W->sc);
     BATCH_LAUNCHED();
-    bprecond_any(h, W, 1, s);
-    int64_t N = (int64_t)nu * K;
-    k_bupdate_p<<<grid_for(N, 256), 256, 0, s>>>(N, K, W->sc, W->Z, W->P);
-    BATCH_LAUNCHED();
+    BSums d{{W->B}, {W->B}, 1};
+    bsums(W, N, d, s);
+    bstage2(h, W, ST_BN, 1, N, 0, s);
 }
 
 static void bphase_step(vemg_hierarchy *h, BatchWork *W, cudaStream_t s, cudaGraphConditionalHandle hd, int use_cond) {
-    bspmv_pq(h, W, s);
-    k_bupdate_xr<<<kBB, kBT, 0, s>>>(h->nu, W->K, W->P, W->Q, W->X, W->R, W->sc, bpart(W, BC_XR), W->ctr + BC_XR, hd,
-                                     use_cond);
+    const int K = W->K;
+    const int64_t N = (int64_t)h->nu * K;
+    bcsr<BOP_SPMV, double, double, double, double, double>(W->Aout, h->nu, nullptr, 0, (const double *)nullptr,
+                                                           (const double *)nullptr, W->P, W->Q, K, nullptr, -1, s);
+    {
+        BSums d{{W->P}, {W->Q}, 1};
+        bsums(W, N, d, s);
+        bstage2(h, W, ST_ALPHA, 1, N, 0, s);
+    }
+    k_bupdate_xr<<<grid_for(N, 256), 256, 0, s>>>(N, K, W->P, W->Q, W->X, W->R, W->sc);
     BATCH_LAUNCHED();
+    {
+        BSums d{{W->R}, {W->R}, 1};
+        bsums(W, N, d, s);
+        bstage2(h, W, ST_RN, 1, N, 0, s, hd, use_cond);
+    }
 }
 
 static void bphase_direction(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
@@ -621,14 +610,20 @@ static void bphase_direction(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
 
 static void bphase_post(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
     const int K = W->K, nu = h->nu;
+    const int64_t N = (int64_t)nu * K;
     if (h->bc == VEMG_NEUMANN) {
-        k_bmean<<<kBB, kBT, 0, s>>>(nu, K, W->X, 1.0 / (double)nu, B_XMEAN, W->sc, bpart(W, BC_SUMX), W->ctr + BC_SUMX);
-        BATCH_LAUNCHED();
-        int64_t N = (int64_t)nu * K;
+        BSums d{{W->X}, {nullptr}, 1};
+        bsums(W, N, d, s);
+        bstage2(h, W, ST_MEAN_X, 1, N, 0, s);
         k_bsub_mean<<<grid_for(N, 256), 256, 0, s>>>(N, K, W->X, W->sc, B_XMEAN);
         BATCH_LAUNCHED();
     }
-    btrue(h, W, s);
+    // true residual into Q
+    bcsr<BOP_RES, double, double, double, double, double>(W->Aout, h->nu, nullptr, 0, (const double *)nullptr, W->B,
+                                                          W->X, W->Q, K, nullptr, -1, s);
+    BSums d{{W->Q}, {W->Q}, 1};
+    bsums(W, N, d, s);
+    bstage2(h, W, ST_TRUE, 1, N, 0, s);
 }
 
 static void release_batch_graphs(BatchWork *W) {
@@ -655,7 +650,6 @@ static void build_batch_graphs(vemg_hierarchy *h, BatchWork *W) {
     try {
         VEMG_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         bphase_pre(h, W, cs);
-        bphase_step(h, W, cs, 0, 0);
         VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &G->gpre));
         G->k_pre = count;
         count = 0;
@@ -681,7 +675,7 @@ static void build_batch_graphs(vemg_hierarchy *h, BatchWork *W) {
         bphase_direction(h, W, cs);
         bphase_step(h, W, cs, G->handle, 1);
         VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &body));
-        G->k_body = count - 1;
+        G->k_body = count - 1;   // k_bcond_init runs once per solve
         G->k_pre += 1;
         count = 0;
         VEMG_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -710,12 +704,74 @@ void release_batch(vemg_hierarchy *h) {
     h->batch = nullptr;
 }
 
+__global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void k_recip(int n, const double *__restrict__ d, void *out, int fp32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = 1.0 / d[i];
+    if (fp32) ((float *)out)[i] = (float)v;
+    else ((double *)out)[i] = v;
+}
+
+static const void *values(Arena &ar, const double *v, int64_t n, bool fp32, cudaStream_t s) {
+    if (!fp32) return v;
+    float *f = ar.alloc<float>(n);
+    if (n > 0) {
+        k_to_f32<<<grid_for(n, 256), 256, 0, s>>>(n, v, f);
+        VEMG_CHECK_LAUNCH();
+    }
+    return f;
+}
+
+static BChain *build_bchain(const Chain &C, bool fp32, Arena &ar, cudaStream_t s) {
+    BChain *B = new BChain();
+    B->nlev = C.nlev;
+    B->direct = C.direct;
+    B->nc = C.nc;
+    B->G = C.G;
+    for (int l = 0; l < C.nlev; ++l) {
+        const Level &L = C.lv[l];
+        BLevel &T = B->lv[l];
+        T.n = L.A.n;
+        T.ncolours = L.ncolours;
+        T.rp = L.A.rp;
+        T.ci = L.A.ci;
+        T.colour = L.colour;
+        T.crow = L.crow;
+        T.cptr = L.cptr;
+        T.v = values(ar, L.A.v, L.A.nnz, fp32, s);
+        void *di = fp32 ? (void *)ar.alloc<float>(L.A.n) : (void *)ar.alloc<double>(L.A.n);
+        k_recip<<<grid_for(L.A.n, 256), 256, 0, s>>>(L.A.n, L.diag, di, fp32);
+        VEMG_CHECK_LAUNCH();
+        T.dinv = di;
+        if (l + 1 < C.nlev) {
+            T.prp = L.P.rp;
+            T.pci = L.P.ci;
+            T.pv = values(ar, L.P.v, L.P.nnz, fp32, s);
+            T.trp = L.PT.rp;
+            T.tci = L.PT.ci;
+            T.tv = values(ar, L.PT.v, L.PT.nnz, fp32, s);
+        }
+    }
+    return B;
+}
+
+BatchWork *new_batch_work(vemg_hierarchy *h, int K, cudaStream_t s);
+
 static BatchWork *batch_work(vemg_hierarchy *h, int K, cudaStream_t s) {
     if (h->batch && h->batch->K == K) return h->batch;
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
     release_batch(h);
+    h->batch = new_batch_work(h, K, s);
+    return h->batch;
+}
+
+BatchWork *new_batch_work(vemg_hierarchy *h, int K, cudaStream_t s) {
     BatchWork *W = new BatchWork();
-    h->batch = W;
     W->K = K;
     Arena &ar = W->arena;
     int64_t N = (int64_t)h->n * K;
@@ -725,19 +781,32 @@ static BatchWork *batch_work(vemg_hierarchy *h, int K, cudaStream_t s) {
     W->P = ar.alloc<double>(N);
     W->Q = ar.alloc<double>(N);
     W->B = ar.alloc<double>(N);
-    size_t es = h->precision == VEMG_PREC_FP32 ? sizeof(float) : sizeof(double);
-    const SChain *chains[2] = {&h->ssurf, &h->sbar};
+    VEMG_CHECK_CUDA(cudaMemsetAsync(W->Q, 0, sizeof(double) * N, s));
+    VEMG_CHECK_CUDA(cudaMemsetAsync(W->Z, 0, sizeof(double) * N, s));
+    const bool fp32 = h->precision == VEMG_PREC_FP32;
+    size_t es = fp32 ? sizeof(float) : sizeof(double);
+    const Chain *chains[2] = {&h->surf, &h->bar};
+    if (h->bc == VEMG_NEUMANN) W->bsurf = build_bchain(h->surf, fp32, ar, s);
+    W->bbar = build_bchain(h->bar, fp32, ar, s);
+    if (h->bc == VEMG_NEUMANN) {
+        W->Aout = CsrP{h->A.rp, h->A.ci, h->A.v};
+        W->caller_of = h->new2old;
+    } else {
+        const DCsr &A0 = h->bar.lv[0].A;
+        W->Aout = CsrP{A0.rp, A0.ci, A0.v};
+        W->caller_of = h->new2old + h->mtop;
+    }
     for (int ch = 0; ch < 2; ++ch)
         for (int l = 0; l < chains[ch]->nlev; ++l) {
-            int64_t m = (int64_t)chains[ch]->lv[l].n * K;
+            int64_t m = (int64_t)chains[ch]->lv[l].A.n * K;
             W->lx[ch][l] = ar.alloc<char>((int64_t)es * m);
             W->lb[ch][l] = ar.alloc<char>((int64_t)es * m);
             W->lr[ch][l] = ar.alloc<char>((int64_t)es * m);
         }
     W->sc = ar.alloc<double>(B_COUNT * K + G_COUNT);
-    W->part = ar.alloc<double>((int64_t)5 * kBB * K * BC_COUNT);
-    W->ctr = ar.alloc<unsigned>(BC_COUNT);
-    VEMG_CHECK_CUDA(cudaMemsetAsync(W->ctr, 0, sizeof(unsigned) * BC_COUNT, s));
+    W->part = ar.alloc<double>((int64_t)5 * stage1_blocks(N) * K);
+    W->ctr = ar.alloc<unsigned>(2);
+    VEMG_CHECK_CUDA(cudaMemsetAsync(W->ctr, 0, sizeof(unsigned) * 2, s));
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
     return W;
 }
@@ -754,7 +823,7 @@ int solve_batch(vemg_hierarchy *h, int k, const double *Bin, int64_t ldb, double
     const int nu = h->nu;
     k_binit<<<1, 1, 0, s>>>(W->sc, K, rtol, max_it);
     BATCH_LAUNCHED();
-    k_bgather<<<grid_for((int64_t)nu * K, 256), 256, 0, s>>>(nu, K, k, ldb, h->caller_of, Bin, W->B);
+    k_bgather<<<grid_for((int64_t)nu * K, 256), 256, 0, s>>>(nu, K, k, ldb, W->caller_of, Bin, W->B);
     BATCH_LAUNCHED();
     if (!W->graphs) build_batch_graphs(h, W);
     BatchGraphs *G = W->graphs;
@@ -765,11 +834,11 @@ int solve_batch(vemg_hierarchy *h, int k, const double *Bin, int64_t ldb, double
     VEMG_CHECK_CUDA(cudaMemcpyAsync(hs.data(), W->sc, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s));
     int ntop = h->bc == VEMG_DIRICHLET_TOP ? h->mtop : 0;
     int64_t nsc = (int64_t)std::max(nu, ntop) * k;
-    k_bscatter<<<grid_for(nsc, 256), 256, 0, s>>>(nu, K, k, ldx, h->caller_of, h->tops, ntop, W->X, Xout);
+    k_bscatter<<<grid_for(nsc, 256), 256, 0, s>>>(nu, K, k, ldx, W->caller_of, h->tops, ntop, W->X, Xout);
     BATCH_LAUNCHED();
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
     int rounds = (int)hs[B_COUNT * K + G_ITERS];
-    h->launches += G->k_pre + G->k_post + (rounds > 1 ? (int64_t)(rounds - 1) * G->k_body : 0);
+    h->launches += G->k_pre + G->k_post + (int64_t)rounds * G->k_body;
     int rc = VEMG_OK;
     for (int c = 0; c < k; ++c) {
         vemg_info &in = infos[c];
@@ -788,3 +857,330 @@ int solve_batch(vemg_hierarchy *h, int k, const double *Bin, int64_t ldb, double
 }
 
 }  // namespace vemg
+
+// ------------------------------------------------------------------------------------------
+// continuous batching: an engine holds K column slots of one hierarchy. A request is admitted into
+// a free slot between iterations (its column is prepared and marked fresh, so its first direction
+// is p = z - mu while the other columns continue their own recurrences); every step advances all
+// occupied slots by whole iterations; a finished slot is retired (x copied out) and reused.
+
+namespace vemg {
+
+struct Engine {
+    vemg_hierarchy *h = nullptr;
+    BatchWork *W = nullptr;
+    cudaStream_t s = nullptr;
+    cudaGraphExec_t step = nullptr;
+    cudaGraph_t gstep = nullptr;
+    int64_t k_step = 0;
+    std::vector<int> used;        // slot occupied
+    double *hsc = nullptr;        // pinned copy of the per-column scalars
+    double *colpart = nullptr;    // single-column reduction partials
+    int ncolblk = 0;
+};
+
+static constexpr int kColBlocks = 128;
+
+// sum over rows of column c of a (or of a^2); per-block partials
+__global__ void k_col_sum(int n, int K, int c, const double *__restrict__ a, int square, double *part) {
+    __shared__ double sh[256];
+    double v = 0.0;
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < n; i += kColBlocks * 256) {
+        double x = a[(int64_t)i * K + c];
+        v += square ? x * x : x;
+    }
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// admission of column c: after the sum of b (mode 0) or of the projected b squared (mode 1)
+__global__ void k_col_admit(int mode, int neumann, double inv_n, int K, int c, const double *__restrict__ part,
+                            double *sc, double tol, int maxit) {
+    double t = 0.0;
+    for (int k = 0; k < kColBlocks; ++k) t += part[k];
+    if (mode == 0) {
+        sc[B_BMEAN * K + c] = neumann ? t * inv_n : 0.0;
+        return;
+    }
+    double bn = sqrt(t);
+    for (int slot = 0; slot < B_COUNT; ++slot)
+        if (slot != B_BMEAN) sc[slot * K + c] = 0.0;
+    sc[B_BN * K + c] = bn;
+    sc[B_TOL * K + c] = tol;
+    sc[B_MAXIT * K + c] = (double)maxit;
+    sc[B_FRESH * K + c] = 1.0;
+    if (bn == 0.0) {
+        sc[B_ZERO * K + c] = 1.0;
+        sc[B_CONV * K + c] = 1.0;
+    }
+}
+
+__global__ void k_col_gather(int nu, int K, int c, const int *__restrict__ caller_of, const double *__restrict__ b,
+                             double *__restrict__ B) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nu) B[(int64_t)i * K + c] = b[caller_of[i]];
+}
+
+// b -= mean, r = b, x = p = z = q = 0 in column c
+__global__ void k_col_prepare(int nu, int K, int c, const double *__restrict__ sc, double *B, double *R, double *X,
+                              double *P, double *Z, double *Q) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nu) return;
+    int64_t e = (int64_t)i * K + c;
+    double bi = B[e] - sc[B_BMEAN * K + c];
+    B[e] = bi;
+    R[e] = bi;
+    X[e] = 0.0;
+    P[e] = 0.0;
+    Z[e] = 0.0;
+    Q[e] = 0.0;
+}
+
+__global__ void k_col_mean(int K, int c, const double *__restrict__ part, double inv_n, double *sc) {
+    double t = 0.0;
+    for (int k = 0; k < kColBlocks; ++k) t += part[k];
+    sc[B_XMEAN * K + c] = t * inv_n;
+}
+
+__global__ void k_col_scatter(int nu, int K, int c, int neumann, const int *__restrict__ caller_of,
+                              const int *__restrict__ tops, int ntop, const double *__restrict__ sc,
+                              const double *__restrict__ X, double *__restrict__ x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double mu = neumann ? sc[B_XMEAN * K + c] : 0.0;
+    if (i < nu) x[caller_of[i]] = X[(int64_t)i * K + c] - mu;
+    if (i < ntop) x[tops[i]] = 0.0;
+}
+
+// a retired slot is frozen (zero right-hand side, converged) until it is admitted again
+__global__ void k_col_free(int nu, int K, int c, double *sc, double *B, double *R, double *X, double *P) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nu) {
+        int64_t e = (int64_t)i * K + c;
+        B[e] = 0.0;
+        R[e] = 0.0;
+        X[e] = 0.0;
+        P[e] = 0.0;
+    }
+    if (i == 0) {
+        for (int slot = 0; slot < B_COUNT; ++slot) sc[slot * K + c] = 0.0;
+        sc[B_ZERO * K + c] = 1.0;
+        sc[B_CONV * K + c] = 1.0;
+    }
+}
+
+__global__ void k_engine_init(double *sc, int K) {
+    for (int i = 0; i < B_COUNT * K + G_COUNT; ++i) sc[i] = 0.0;
+    for (int c = 0; c < K; ++c) {
+        sc[B_ZERO * K + c] = 1.0;
+        sc[B_CONV * K + c] = 1.0;
+    }
+}
+
+BatchWork *new_batch_work(vemg_hierarchy *h, int K, cudaStream_t s);
+
+}  // namespace vemg
+
+using namespace vemg;
+
+struct vemg_engine : vemg::Engine {};
+
+extern "C" {
+
+int vemg_engine_create(vemg_hierarchy *h, int slots, void *stream, vemg_engine **out) {
+    if (!h || !out || slots < 1 || slots > kMaxK) return VEMG_EINVAL;
+    *out = nullptr;
+    vemg_engine *e = new vemg_engine();
+    try {
+        cudaStream_t s = (cudaStream_t)stream;
+        prepare_solve(h, s);
+        int K = 1;
+        while (K < slots) K *= 2;
+        e->h = h;
+        e->s = s;
+        e->W = new_batch_work(h, K, s);
+        e->used.assign(K, 0);
+        VEMG_CHECK_CUDA(cudaMallocHost(&e->hsc, sizeof(double) * (B_COUNT * K + G_COUNT)));
+        e->colpart = e->W->arena.alloc<double>(kColBlocks);
+        k_engine_init<<<1, 1, 0, s>>>(e->W->sc, K);
+        VEMG_CHECK_LAUNCH();
+        // one iteration of every occupied column, as a graph
+        cudaStream_t cs;
+        VEMG_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        int64_t count = 0;
+        b_count = &count;
+        VEMG_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        bphase_direction(h, e->W, cs);
+        bphase_step(h, e->W, cs, 0, 0);
+        VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &e->gstep));
+        b_count = nullptr;
+        e->k_step = count;
+        VEMG_CHECK_CUDA(cudaStreamDestroy(cs));
+        VEMG_CHECK_CUDA(cudaGraphInstantiate(&e->step, e->gstep, 0));
+        VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+    } catch (const Error &err) {
+        b_count = nullptr;
+        vemg_engine_destroy(e);
+        return err.code;
+    } catch (...) {
+        b_count = nullptr;
+        vemg_engine_destroy(e);
+        return VEMG_EINTERNAL;
+    }
+    *out = e;
+    return VEMG_OK;
+}
+
+void vemg_engine_destroy(vemg_engine *e) {
+    if (!e) return;
+    if (e->s) cudaStreamSynchronize(e->s);
+    if (e->step) cudaGraphExecDestroy(e->step);
+    if (e->gstep) cudaGraphDestroy(e->gstep);
+    if (e->hsc) cudaFreeHost(e->hsc);
+    if (e->W) {
+        e->W->arena.release();
+        delete e->W;
+    }
+    delete e;
+}
+
+int vemg_engine_admit(vemg_engine *e, const double *b_dev, double rtol, int max_it, int *slot) {
+    if (!e || !b_dev || !slot || !(rtol >= 0.0) || max_it < 0) return VEMG_EINVAL;
+    int c = -1;
+    for (int k = 0; k < (int)e->used.size(); ++k)
+        if (!e->used[k]) {
+            c = k;
+            break;
+        }
+    if (c < 0) return VEMG_ENOMEM;
+    try {
+        vemg_hierarchy *h = e->h;
+        BatchWork *W = e->W;
+        const int nu = h->nu, K = W->K;
+        const bool neu = h->bc == VEMG_NEUMANN;
+        cudaStream_t s = e->s;
+        k_col_gather<<<grid_for(nu, 256), 256, 0, s>>>(nu, K, c, W->caller_of, b_dev, W->B);
+        VEMG_CHECK_LAUNCH();
+        k_col_sum<<<kColBlocks, 256, 0, s>>>(nu, K, c, W->B, 0, e->colpart);
+        VEMG_CHECK_LAUNCH();
+        k_col_admit<<<1, 1, 0, s>>>(0, neu, 1.0 / nu, K, c, e->colpart, W->sc, rtol, max_it);
+        VEMG_CHECK_LAUNCH();
+        k_col_prepare<<<grid_for(nu, 256), 256, 0, s>>>(nu, K, c, W->sc, W->B, W->R, W->X, W->P, W->Z, W->Q);
+        VEMG_CHECK_LAUNCH();
+        k_col_sum<<<kColBlocks, 256, 0, s>>>(nu, K, c, W->B, 1, e->colpart);
+        VEMG_CHECK_LAUNCH();
+        k_col_admit<<<1, 1, 0, s>>>(1, neu, 1.0 / nu, K, c, e->colpart, W->sc, rtol, max_it);
+        VEMG_CHECK_LAUNCH();
+        h->launches += 6;
+    } catch (const Error &err) {
+        return err.code;
+    }
+    e->used[c] = 1;
+    *slot = c;
+    return VEMG_OK;
+}
+
+int vemg_engine_launch(vemg_engine *e, int iters) {
+    if (!e || iters < 0) return VEMG_EINVAL;
+    for (int k = 0; k < iters; ++k) {
+        cudaError_t err = cudaGraphLaunch(e->step, e->s);
+        if (err != cudaSuccess) {
+            set_last_cuda_error(err, "cudaGraphLaunch", __FILE__, __LINE__);
+            return VEMG_ECUDA;
+        }
+    }
+    e->h->launches += (int64_t)iters * e->k_step;
+    const int K = e->W->K;
+    cudaError_t err = cudaMemcpyAsync(e->hsc, e->W->sc, sizeof(double) * (B_COUNT * K + G_COUNT),
+                                      cudaMemcpyDeviceToHost, e->s);
+    if (err != cudaSuccess) {
+        set_last_cuda_error(err, "cudaMemcpyAsync", __FILE__, __LINE__);
+        return VEMG_ECUDA;
+    }
+    return VEMG_OK;
+}
+
+int vemg_engine_wait(vemg_engine *e) {
+    if (!e) return VEMG_EINVAL;
+    cudaError_t err = cudaStreamSynchronize(e->s);
+    if (err != cudaSuccess) {
+        set_last_cuda_error(err, "cudaStreamSynchronize", __FILE__, __LINE__);
+        return VEMG_ECUDA;
+    }
+    return VEMG_OK;
+}
+
+int vemg_engine_poll(const vemg_engine *e, int slot, vemg_info *info, int *state) {
+    if (!e || !state || slot < 0 || slot >= (int)e->used.size()) return VEMG_EINVAL;
+    if (!e->used[slot]) {
+        *state = VEMG_SLOT_FREE;
+        return VEMG_OK;
+    }
+    const int K = e->W->K;
+    const double *sc = e->hsc;
+    bool conv = sc[B_CONV * K + slot] != 0.0, flag = sc[B_FLAG * K + slot] != 0.0;
+    bool out = sc[B_ITERS * K + slot] >= sc[B_MAXIT * K + slot];
+    *state = (conv || flag || out) ? VEMG_SLOT_DONE : VEMG_SLOT_RUNNING;
+    if (info) {
+        double bn = sc[B_BN * K + slot];
+        info->iters = (int)sc[B_ITERS * K + slot];
+        info->relres = bn > 0.0 ? sc[B_RN * K + slot] / bn : 0.0;
+        info->true_relres = -1.0;
+        info->b_mean = sc[B_BMEAN * K + slot];
+        info->status = sc[B_ZERO * K + slot] != 0.0 ? VEMG_OK
+                       : flag                       ? VEMG_EBREAKDOWN
+                       : conv                       ? VEMG_OK
+                                                    : VEMG_ENOTCONV;
+    }
+    return VEMG_OK;
+}
+
+int vemg_engine_retire(vemg_engine *e, int slot, double *x_dev) {
+    if (!e || !x_dev || slot < 0 || slot >= (int)e->used.size() || !e->used[slot]) return VEMG_EINVAL;
+    try {
+        vemg_hierarchy *h = e->h;
+        BatchWork *W = e->W;
+        const int nu = h->nu, K = W->K;
+        const bool neu = h->bc == VEMG_NEUMANN;
+        cudaStream_t s = e->s;
+        if (neu) {
+            k_col_sum<<<kColBlocks, 256, 0, s>>>(nu, K, slot, W->X, 0, e->colpart);
+            VEMG_CHECK_LAUNCH();
+            k_col_mean<<<1, 1, 0, s>>>(K, slot, e->colpart, 1.0 / nu, W->sc);
+            VEMG_CHECK_LAUNCH();
+        }
+        int ntop = neu ? 0 : h->mtop;
+        k_col_scatter<<<grid_for(std::max(nu, ntop), 256), 256, 0, s>>>(nu, K, slot, neu, W->caller_of, h->tops, ntop,
+                                                                         W->sc, W->X, x_dev);
+        VEMG_CHECK_LAUNCH();
+        k_col_free<<<grid_for(nu, 256), 256, 0, s>>>(nu, K, slot, W->sc, W->B, W->R, W->X, W->P);
+        VEMG_CHECK_LAUNCH();
+        VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+        h->launches += neu ? 4 : 2;
+    } catch (const Error &err) {
+        return err.code;
+    }
+    e->used[slot] = 0;
+    return VEMG_OK;
+}
+
+int vemg_engine_slots(const vemg_engine *e, int *slots, int *free_slots) {
+    if (!e || !slots || !free_slots) return VEMG_EINVAL;
+    *slots = (int)e->used.size();
+    int f = 0;
+    for (int u : e->used) f += !u;
+    *free_slots = f;
+    return VEMG_OK;
+}
+
+int vemg_engine_bytes(const vemg_engine *e, size_t *bytes) {
+    if (!e || !bytes) return VEMG_EINVAL;
+    *bytes = e->W->arena.bytes;
+    return VEMG_OK;
+}
+
+}  // extern "C"

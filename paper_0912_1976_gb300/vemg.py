@@ -79,6 +79,15 @@ PROTOTYPES = {
     "vemg_precond": (C.c_int, [_VP, _DP, _DP, _VP]),
     "vemg_vcycle": (C.c_int, [_VP, C.c_int, _DP, _DP, _VP]),
     "vemg_spmv_static": (C.c_int, [_VP, _DP, _DP, _VP]),
+    "vemg_engine_create": (C.c_int, [_VP, C.c_int, _VP, C.POINTER(C.c_void_p)]),
+    "vemg_engine_destroy": (None, [_VP]),
+    "vemg_engine_admit": (C.c_int, [_VP, _DP, C.c_double, C.c_int, C.POINTER(C.c_int)]),
+    "vemg_engine_launch": (C.c_int, [_VP, C.c_int]),
+    "vemg_engine_wait": (C.c_int, [_VP]),
+    "vemg_engine_poll": (C.c_int, [_VP, C.c_int, C.POINTER(vemg_info), C.POINTER(C.c_int)]),
+    "vemg_engine_retire": (C.c_int, [_VP, C.c_int, _DP]),
+    "vemg_engine_slots": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "vemg_engine_bytes": (C.c_int, [_VP, C.POINTER(C.c_size_t)]),
     "vemg_probe": (C.c_int, [_VP, C.c_int]),
     "vemg_kernel_launches": (C.c_int, [_VP, C.POINTER(C.c_int64)]),
     "vemg_probe_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
@@ -392,3 +401,61 @@ def vemg_spmv_static(h: Hierarchy, x_dev, y_dev=None, stream=None):
         y_dev = torch.empty_like(x_dev)
     _check(lib().vemg_spmv_static(h.h, _dev(x_dev), _dev(y_dev), _stream(stream)), "vemg_spmv_static")
     return y_dev
+
+
+# ------------------------------------------------------------------------------------------
+# continuous batching engine
+
+VEMG_SLOT_FREE, VEMG_SLOT_RUNNING, VEMG_SLOT_DONE = 0, 1, 2
+
+
+class Engine:
+    """K right-hand-side slots of one hierarchy; requests join and leave between iterations."""
+
+    def __init__(self, h: Hierarchy, slots: int, stream=None):
+        self.hier = h
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        out = C.c_void_p()
+        _check(lib().vemg_engine_create(h.h, slots, C.c_void_p(self.stream.cuda_stream), C.byref(out)),
+               "vemg_engine_create")
+        self.e = out
+        n, f = C.c_int(), C.c_int()
+        lib().vemg_engine_slots(self.e, C.byref(n), C.byref(f))
+        self.slots = n.value
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        if getattr(self, "e", None) and self.e.value:
+            lib().vemg_engine_destroy(self.e)
+            self.e = C.c_void_p(None)
+
+    def admit(self, b_dev: torch.Tensor, rtol=1e-8, max_it=1000) -> int:
+        slot = C.c_int()
+        _check(lib().vemg_engine_admit(self.e, _dev(b_dev), rtol, max_it, C.byref(slot)), "vemg_engine_admit")
+        return slot.value
+
+    def launch(self, iters=1):
+        _check(lib().vemg_engine_launch(self.e, iters), "vemg_engine_launch")
+
+    def wait(self):
+        _check(lib().vemg_engine_wait(self.e), "vemg_engine_wait")
+
+    def poll(self, slot):
+        info, st = vemg_info(), C.c_int()
+        _check(lib().vemg_engine_poll(self.e, slot, C.byref(info), C.byref(st)), "vemg_engine_poll")
+        return st.value, info.as_dict()
+
+    def retire(self, slot, x_dev: torch.Tensor):
+        _check(lib().vemg_engine_retire(self.e, slot, _dev(x_dev)), "vemg_engine_retire")
+
+    def free_slots(self) -> int:
+        n, f = C.c_int(), C.c_int()
+        _check(lib().vemg_engine_slots(self.e, C.byref(n), C.byref(f)), "vemg_engine_slots")
+        return f.value
+
+    def bytes(self) -> int:
+        v = C.c_size_t()
+        _check(lib().vemg_engine_bytes(self.e, C.byref(v)), "vemg_engine_bytes")
+        return int(v.value)

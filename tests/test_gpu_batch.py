@@ -1,0 +1,75 @@
+"""Batched solves (vemg_solve_batch): K right-hand sides in one interleaved solve, each column
+with its own Krylov scalars and convergence test. Each column must give what a single solve of
+that right-hand side gives (within the FP64 reordering tolerance) and what the oracle gives."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_0912_1976_gb300 import inputs as I
+from paper_0912_1976_gb300 import vemg as V
+
+pytestmark = pytest.mark.gpu
+
+_cache = {}
+
+
+def _setup(bc=V.VEMG_NEUMANN, precision=V.VEMG_PREC_FP64):
+    key = (bc, precision)
+    if key not in _cache:
+        m = I.make_mesh(32, 28, 16, I.depth_sines(1e-3), z_jitter=0.3, seed=41)
+        vm = V.Mesh.from_inputs(m)
+        A = V.vemg_assemble(vm)
+        h = V.vemg_setup(A, vm, V.vemg_default_options(bc=bc, precision=precision))
+        _cache[key] = (m, vm, A, h)
+    return _cache[key]
+
+
+def _rhs(n, k, seed):
+    return torch.from_numpy(np.stack([I.normal_loads(n, seed + c) for c in range(k)])).cuda()
+
+
+@pytest.mark.parametrize("k", [1, 3, 8, 33])
+@pytest.mark.parametrize("precision", [V.VEMG_PREC_FP64, V.VEMG_PREC_FP32])
+def test_batch_columns_equal_single_solves(k, precision):
+    m, vm, A, h = _setup(precision=precision)
+    B = _rhs(m.n, k, 100)
+    X, infos = V.vemg_solve_batch(h, B, rtol=1e-9, max_it=300)
+    for c in range(k):
+        x1, i1 = V.vemg_solve(h, B[c].contiguous(), rtol=1e-9, max_it=300)
+        assert infos[c]["status"] == "OK"
+        assert abs(infos[c]["iters"] - i1["iters"]) <= 1
+        if infos[c]["iters"] == i1["iters"]:
+            err = (X[c] - x1).norm().item() / x1.norm().item()
+            assert err <= (1e-9 if precision == V.VEMG_PREC_FP64 else 1e-6), (c, err)
+        assert infos[c]["true_relres"] <= 2e-9
+
+
+def test_batch_matches_oracle_and_handles_zero_columns():
+    m, vm, A, h = _setup()
+    k = 5
+    B = _rhs(m.n, k, 200)
+    B[2].zero_()                                   # a zero right-hand side: x = 0, no iterations
+    X, infos = V.vemg_solve_batch(h, B, rtol=1e-10, max_it=300)
+    om = O.Problem(m)
+    for c in range(k):
+        if c == 2:
+            assert infos[c]["iters"] == 0 and infos[c]["status"] == "OK"
+            assert torch.all(X[c] == 0)
+            continue
+        ro = om.solve(B[c].cpu().numpy(), tol=1e-10)
+        assert abs(infos[c]["iters"] - ro["iters"]) <= 1
+        err = np.linalg.norm(X[c].cpu().numpy() - ro["x"]) / np.linalg.norm(ro["x"])
+        assert err <= 1e-9, (c, err)
+
+
+def test_batch_dirichlet_top():
+    m, vm, A, h = _setup(bc=V.VEMG_DIRICHLET_TOP)
+    B = _rhs(m.n, 4, 300)
+    X, infos = V.vemg_solve_batch(h, B, rtol=1e-9, max_it=300)
+    tops = torch.from_numpy((m.tags & I.TAG_TOP) != 0).cuda()
+    for c in range(4):
+        x1, i1 = V.vemg_solve(h, B[c].contiguous(), rtol=1e-9, max_it=300)
+        assert infos[c]["status"] == "OK" and abs(infos[c]["iters"] - i1["iters"]) <= 1
+        assert torch.all(X[c][tops] == 0)
+        assert (X[c] - x1).norm().item() <= 1e-8 * x1.norm().item()
