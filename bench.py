@@ -44,6 +44,11 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="serving workload: this many Poisson-arrival requests (512 for the full stream)")
+    ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (0: 0.8 x saturation)")
+    ap.add_argument("--case", default="",
+                    help="profiling case NXxNYxNZ (z-jitter 0.3, eps 1e-3): two untimed solves, then exit")
     ap.add_argument("--rhs", type=int, default=0,
                     help="right-hand sides per step (0: the workload's own count); >1 uses vemg_solve_batch")
     return ap.parse_args()
@@ -284,10 +289,81 @@ def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe):
     return out
 
 
+def run_serve(args):
+    """Continuous batching over the serving stream: a saturation run (all requests at t = 0) gives
+    the capacity, then the Poisson run at 80% of it (or --rate) gives the latency percentiles."""
+    import torch
+    from paper_0912_1976_gb300 import serve as S
+    from paper_0912_1976_gb300 import vemg as V
+    prec = V.VEMG_PREC_FP64 if args.precision == "fp64" else V.VEMG_PREC_FP32
+    fac = S.GpuFactory(slots=8, precision=prec)
+    for i in range(len(S.SIZES)):                  # meshes are inputs: generated before the clock
+        fac.mesh(i, 1.0)
+    out = {}
+    rate = args.rate
+    for phase in (["saturation", "poisson"] if not rate else ["poisson"]):
+        reqs = S.make_requests(args.serve, rate=None if phase == "saturation" else rate, seed=5000)
+        srv = S.Server(fac.build, fac.estimate, fac.free_bytes, fac.rhs, new_x=fac.new_x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = srv.run(reqs)
+        torch.cuda.synchronize()
+        span = time.perf_counter() - t0
+        out[phase] = dict(S.summarize(done, span), **srv.stats)
+        if phase == "saturation":
+            rate = 0.8 * out[phase]["requests_per_s"]
+        for e in list(srv.cache.values()):
+            srv._evict(e)
+    p = out["poisson"]
+    line = {"metric": "serving: solves/s at FP64 rel-res 1e-8, p50/p99 latency", "value": p["solves_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "steps": args.serve, "warmup": 0,
+            "ms_per_step": 1000.0 * p["makespan_s"] / max(p["requests"], 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f64 outer + f32 preconditioner", "data": "synthetic",
+            "config": {"workload": f"serve{args.serve}: Poisson arrivals at {rate:.2f}/s over 8 meshes "
+                                   "(44..399 squared x 24 layers, z-jitter 0.3), eps in {1e-4,1e-3,1e-2,1e-1}, "
+                                   "Neumann/Dirichlet-top 50/50, 1-8 RHS per request, 8-slot engines, rtol 1e-8",
+                       "precision": args.precision},
+            "p50_latency_ms": p["p50_latency_ms"], "p99_latency_ms": p["p99_latency_ms"],
+            "requests_per_s": p["requests_per_s"], "serving": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_case(args):
+    """A small case for ncu captures: build the mesh, set up, run two solves."""
+    import torch
+    from paper_0912_1976_gb300 import inputs as I
+    from paper_0912_1976_gb300 import vemg as V
+    nx, ny, nz = (int(v) for v in args.case.split("x"))
+    m = I.make_mesh(nx, ny, nz, I.depth_sines(1e-3), z_jitter=0.3, seed=77)
+    vm = V.Mesh.from_inputs(m)
+    A = V.vemg_assemble(vm)
+    prec = V.VEMG_PREC_FP64 if args.precision == "fp64" else V.VEMG_PREC_FP32
+    h = V.vemg_setup(A, vm, V.vemg_default_options(precision=prec))
+    kr = max(args.rhs, 1)
+    if kr == 1:
+        b = torch.from_numpy(I.normal_loads(m.n, 5)).cuda()
+        for _ in range(2):
+            _, info = V.vemg_solve(h, b, rtol=RTOL)
+    else:
+        B = torch.from_numpy(I.normal_loads(m.n, 5, k=kr)).cuda()
+        for _ in range(2):
+            _, infos = V.vemg_solve_batch(h, B, rtol=RTOL)
+        info = infos[0]
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "n": m.n, "precision": args.precision, "rhs": kr, "info": info}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args)
+    if args.serve:
+        return run_serve(args)
     import torch
     from paper_0912_1976_gb300 import inputs as I
     from paper_0912_1976_gb300 import vemg as V

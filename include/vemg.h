@@ -150,7 +150,9 @@ int vemg_solve_host(vemg_hierarchy *h, const double *b_host, double *x_host, dou
 
 /* Solve k systems A X = B with one right-hand side per column: column c of B is
    B_dev[c * ldb + i], i < n_nodes (caller order), and likewise X. Each column is an independent
-   CG/FCG run with its own step lengths and convergence test; a converged column is frozen.
+   CG/FCG run with its own step lengths and convergence test; a converged column is frozen. A column
+   whose best residual has not dropped by 1% in 30 iterations has reached the round-off floor and
+   stops with VEMG_ENOTCONV (relres holds its last residual).
    infos has k entries. Returns VEMG_OK if every column converged, else the first non-OK
    column status. */
 int vemg_solve_batch(vemg_hierarchy *h, int k, const double *B_dev, int64_t ldb, double *X_dev,

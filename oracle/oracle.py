@@ -18,6 +18,8 @@ LIB = os.path.join(HERE, "liboracle.so")
 
 BC_NEUMANN = 0
 BC_DIRICHLET_TOP = 1
+# the three preconditioners of section 6
+PC_ADDITIVE, PC_VL_SOR, PC_SA = 0, 1, 2
 STATUS = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ENOTCONV", 5: "EBREAKDOWN"}
 
 # the paper's smoothed-aggregation parameters (section 6)
@@ -47,7 +49,7 @@ def lib():
         dp, ip, u8p = C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_uint8)
         L.or_setup.restype = C.c_void_p
         L.or_setup.argtypes = [C.c_int, dp, C.c_int, ip, u8p, C.c_int, ip, C.c_int, C.c_double,
-                               C.c_double, C.c_int, C.c_int, C.c_int, ip]
+                               C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, ip]
         L.or_free.argtypes = [C.c_void_p]
         L.or_size.restype = C.c_long
         L.or_size.argtypes = [C.c_void_p, C.c_char_p, C.c_int, C.c_int]
@@ -87,7 +89,7 @@ class Problem:
     """Oracle setup of one mesh: ordering, A, E~, E~^T A E~, and the two SA chains."""
 
     def __init__(self, mesh, bc: int = BC_NEUMANN, theta=THETA, omega_p=OMEGA_P, coarse_max=COARSE_MAX,
-                 max_levels=MAX_LEVELS, natural_order=False):
+                 max_levels=MAX_LEVELS, natural_order=False, precond=PC_ADDITIVE):
         L = lib()
         self._keep = (_f64(mesh.xyz), _i32(mesh.tets), np.ascontiguousarray(mesh.tags, dtype=np.uint8),
                       _i32(mesh.top_tris))
@@ -95,7 +97,7 @@ class Problem:
         st = C.c_int(0)
         self.h = L.or_setup(xyz.shape[0], _p(xyz, C.c_double), tets.shape[0], _p(tets, C.c_int),
                             _p(tags, C.c_uint8), tris.shape[0], _p(tris, C.c_int), bc, theta, omega_p,
-                            coarse_max, max_levels, int(natural_order), C.byref(st))
+                            coarse_max, max_levels, int(natural_order), precond, C.byref(st))
         if not self.h:
             raise OracleError(f"or_setup failed: {STATUS.get(st.value, st.value)}")
         self.bc = bc

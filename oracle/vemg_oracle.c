@@ -52,6 +52,11 @@
 #define BC_NEUMANN 0
 #define BC_DIRICHLET_TOP 1
 
+/* the three preconditioners compared in section 6 */
+#define PC_ADDITIVE 0   /* vertical lumping + additive smoother, Eq. ourpreconditioner (section 5.5) */
+#define PC_VL_SOR 1     /* vertical lumping as the first coarsening of a V-cycle with SOR smoothing on A */
+#define PC_SA 2         /* smoothed-aggregation AMG on A */
+
 #define MAX_LEVELS_CAP 16
 
 /* ------------------------------------------------------------------------------------------ */
@@ -696,6 +701,8 @@ typedef struct {
     csr Ac;              /* E~^T A E~ */
     chain surf;          /* SA chain on Ac (Neumann only) */
     chain bar;           /* SA chain on A_bar */
+    int precond;         /* PC_ADDITIVE, PC_VL_SOR or PC_SA */
+    chain one;           /* the single chain of PC_VL_SOR / PC_SA */
     /* copy of the mesh needed for the load vector */
     int ntet;
     int *tets;
@@ -972,12 +979,15 @@ void or_free(void *hp);
 
 void *or_setup(int n, const double *xyz, int ntet, const int *tets, const unsigned char *tags, int ntri,
                const int *tris, int bc, double theta, double omega_p, int coarse_max, int max_levels,
-               int natural_order, int *status) {
+               int natural_order, int precond, int *status) {
     *status = OR_OK;
-    if (n <= 0 || ntet <= 0 || (bc != BC_NEUMANN && bc != BC_DIRICHLET_TOP)) { *status = OR_EINVAL; return NULL; }
+    if (n <= 0 || ntet <= 0 || (bc != BC_NEUMANN && bc != BC_DIRICHLET_TOP) || precond < PC_ADDITIVE ||
+        precond > PC_SA || (precond == PC_VL_SOR && bc != BC_NEUMANN)) { *status = OR_EINVAL; return NULL; }
     for (int e = 0; e < 4 * ntet; ++e) if (tets[e] < 0 || tets[e] >= n) { *status = OR_EMESH; return NULL; }
     problem *h = (problem *)xcalloc(1, sizeof(problem));
     h->n = n; h->bc = bc; h->ntet = ntet;
+    /* with Dirichlet on top, smoothed aggregation on A_bar is the additive preconditioner itself */
+    h->precond = bc == BC_DIRICHLET_TOP ? PC_ADDITIVE : precond;
     h->tets = (int *)xcalloc((size_t)ntet * 4, sizeof(int));
     memcpy(h->tets, tets, sizeof(int) * (size_t)ntet * 4);
     h->xyz = (double *)xcalloc((size_t)n * 3, sizeof(double));
@@ -996,6 +1006,27 @@ void *or_setup(int n, const double *xyz, int ntet, const int *tets, const unsign
     }
     rc = chain_build(&h->bar, Abar, 0, theta, omega_p, coarse_max, max_levels, natural_order);
     if (rc) { or_free(h); *status = rc; return NULL; }
+    if (h->precond == PC_SA) {
+        rc = chain_build(&h->one, csr_copy(&h->A), 1, theta, omega_p, coarse_max, max_levels, natural_order);
+        if (rc) { or_free(h); *status = rc; return NULL; }
+    } else if (h->precond == PC_VL_SOR) {
+        /* level 0: A with the vertical extrapolation E~ as its prolongator; below it, the SA chain
+           of E~^T A E~ (section 6: "the vertical lumping of the equation is simply the first of a
+           multilevel multigrid cycle") */
+        chain *V = &h->one, *S = &h->surf;
+        memset(V, 0, sizeof(*V));
+        if (S->nlev + 1 > MAX_LEVELS_CAP) { or_free(h); *status = OR_EINVAL; return NULL; }
+        V->singular = 1;
+        V->natural = natural_order;
+        V->nlev = S->nlev + 1;
+        V->lv[0].A = csr_copy(&h->A);
+        V->lv[0].P = csr_copy(&h->E);
+        V->lv[0].PT = csr_copy(&h->ET);
+        for (int l = 0; l < S->nlev; ++l) V->lv[l + 1] = S->lv[l];
+        V->direct = S->direct; V->nc = S->nc; V->Lc = S->Lc; V->sigma = S->sigma;
+        memset(S, 0, sizeof(*S));
+        level_colour(&V->lv[0]);
+    }
     h->wr = (double *)xcalloc((size_t)n, sizeof(double));
     h->wz = (double *)xcalloc((size_t)n, sizeof(double));
     h->wq = (double *)xcalloc((size_t)n, sizeof(double));
@@ -1011,7 +1042,7 @@ void or_free(void *hp) {
     free(h->new2old); free(h->old2new);
     csr_del(&h->A); csr_del(&h->E); csr_del(&h->ET); csr_del(&h->Ac);
     free(h->tri_of); free(h->bary);
-    chain_free(&h->surf); chain_free(&h->bar);
+    chain_free(&h->surf); chain_free(&h->bar); chain_free(&h->one);
     free(h->tets); free(h->xyz);
     free(h->wr); free(h->wz); free(h->wq); free(h->wp); free(h->wx); free(h->wb);
     free(h);
@@ -1027,6 +1058,7 @@ void or_precond(void *hp, const double *r, double *z) {
     problem *h = (problem *)hp;
     int mt = h->mtop, n = h->n;
     if (h->bc == BC_DIRICHLET_TOP) { vcycle(&h->bar, 0, r, z); return; }
+    if (h->precond != PC_ADDITIVE) { vcycle(&h->one, 0, r, z); return; }
     level *s0 = &h->surf.lv[0];
     csr_spmv(&h->ET, r, s0->b);
     vcycle(&h->surf, 0, s0->b, s0->x);
@@ -1126,7 +1158,9 @@ int or_load(void *hp, const double *f, double *b) {
 /* ------------------------------------------------------------------------------------------ */
 /* introspection for tests                                                                     */
 
-static const chain *pick_chain(const problem *h, int which) { return which == 0 ? &h->surf : &h->bar; }
+static const chain *pick_chain(const problem *h, int which) {
+    return which == 0 ? &h->surf : which == 2 ? &h->one : &h->bar;
+}
 
 /* sizes: key in {"n","mtop","nnzA","nnzE","nnzAc","nlev","lev.n","lev.nnz","lev.nnzP",
    "lev.ncolours","direct"} */

@@ -35,8 +35,12 @@ static thread_local int64_t *b_count = nullptr;
 // per-column scalar slots (sc[slot * K + c])
 enum {
     B_RZ = 0, B_PQ, B_ALPHA, B_BETA, B_MU, B_BN, B_RN, B_FLAG, B_ITERS, B_CONV, B_ZERO, B_TRUE, B_BMEAN, B_XMEAN,
-    B_TOL, B_MAXIT, B_FRESH, B_COUNT
+    B_TOL, B_MAXIT, B_FRESH, B_BEST, B_LASTIMP, B_STALL, B_COUNT
 };
+
+// a column whose best residual has not dropped by 1% in this many iterations has reached the
+// round-off floor: it stops (status VEMG_ENOTCONV with its last residual)
+static constexpr int kStallIters = 30;
 // global scalars after the per-column block (g[slot])
 enum { G_TOL = 0, G_MAXIT, G_CONT, G_ITERS, G_COUNT };
 
@@ -342,7 +346,7 @@ __global__ void __launch_bounds__(256) k_bstage2(int op, int nblk, int ns, int K
     if (t == 0) {
         // converged, broken down, or out of iterations: frozen while other columns continue
         bool frozen = sc[B_CONV * K + c] != 0.0 || sc[B_FLAG * K + c] != 0.0 ||
-                      sc[B_ITERS * K + c] >= sc[B_MAXIT * K + c];
+                      sc[B_ITERS * K + c] >= sc[B_MAXIT * K + c] || sc[B_STALL * K + c] != 0.0;
         switch (op) {
             case ST_MEAN_B: sc[B_BMEAN * K + c] = tot[0] * inv_n; break;
             case ST_MEAN_X: sc[B_XMEAN * K + c] = tot[0] * inv_n; break;
@@ -381,7 +385,14 @@ __global__ void __launch_bounds__(256) k_bstage2(int op, int nblk, int ns, int K
                     sc[B_ITERS * K + c] += 1.0;
                     if (!(rn == rn)) sc[B_FLAG * K + c] = 1.0;
                     else if (rn <= sc[B_TOL * K + c] * sc[B_BN * K + c]) sc[B_CONV * K + c] = 1.0;
-                    if (sc[B_CONV * K + c] == 0.0 && sc[B_FLAG * K + c] == 0.0 &&
+                    double best = sc[B_BEST * K + c];
+                    if (best == 0.0 || rn < 0.99 * best) {
+                        sc[B_BEST * K + c] = rn;
+                        sc[B_LASTIMP * K + c] = sc[B_ITERS * K + c];
+                    } else if (sc[B_ITERS * K + c] - sc[B_LASTIMP * K + c] >= kStallIters) {
+                        sc[B_STALL * K + c] = 1.0;
+                    }
+                    if (sc[B_CONV * K + c] == 0.0 && sc[B_FLAG * K + c] == 0.0 && sc[B_STALL * K + c] == 0.0 &&
                         sc[B_ITERS * K + c] < sc[B_MAXIT * K + c])
                         atomicOr(active, 1);
                 }
@@ -1123,7 +1134,7 @@ int vemg_engine_poll(const vemg_engine *e, int slot, vemg_info *info, int *state
     const int K = e->W->K;
     const double *sc = e->hsc;
     bool conv = sc[B_CONV * K + slot] != 0.0, flag = sc[B_FLAG * K + slot] != 0.0;
-    bool out = sc[B_ITERS * K + slot] >= sc[B_MAXIT * K + slot];
+    bool out = sc[B_ITERS * K + slot] >= sc[B_MAXIT * K + slot] || sc[B_STALL * K + slot] != 0.0;
     *state = (conv || flag || out) ? VEMG_SLOT_DONE : VEMG_SLOT_RUNNING;
     if (info) {
         double bn = sc[B_BN * K + slot];

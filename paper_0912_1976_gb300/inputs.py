@@ -234,3 +234,13 @@ def make_workload_mesh(name: str, **over) -> Mesh:
     w.update(over)
     return make_mesh(w["nx"], w["ny"], w["nz"], depth_fn(w["depth"]), z_jitter=w["z_jitter"],
                      xy_jitter=w["xy_jitter"], seed=w["seed"])
+
+
+def scale_depth(mesh: Mesh, factor: float) -> Mesh:
+    """The same mesh with every depth multiplied by `factor`. The generator's z coordinates (layers
+    and z-jitter) are all proportional to the depth scale, so a mesh generated with depth scale 1
+    and scaled by eps is the mesh generated with depth scale eps."""
+    xyz = mesh.xyz.copy()
+    xyz[:, 2] *= factor
+    return Mesh(xyz=xyz, tets=mesh.tets, tags=mesh.tags, top_tris=mesh.top_tris, nx=mesh.nx, ny=mesh.ny,
+                nz=mesh.nz, redraw_passes=mesh.redraw_passes)
