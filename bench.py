@@ -34,6 +34,9 @@ RTOL = 1e-8
 METRIC = "solves/s at FP64 rel-res 1e-8"
 
 
+PRECONDS = {"additive": 0, "vl_sor": 1, "sa": 2}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -41,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vemg", choices=["vemg", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--precond", default="additive", choices=list(PRECONDS),
+                    help="additive (the paper's preconditioner), vl_sor or sa (its two comparison forms)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
@@ -181,7 +186,7 @@ def workload_config(args, n):
     return {"workload": f"{args.workload}: {w['nx']}x{w['ny']}x{w['nz']} extruded hex->6 tets, {n} nodes, "
                         f"H0 {w['depth'][1]:g}, z-jitter {w['z_jitter']}, xy-jitter {w['xy_jitter']}, "
                         f"all-Neumann, N(0,1) loads mean-zero, rtol {RTOL:g}",
-            "precision": args.precision, "rhs_per_step": kr,
+            "precision": args.precision, "preconditioner": args.precond, "rhs_per_step": kr,
             "l2": "inputs larger than L2 (A alone 0.39 GB; no flush needed)",
             "parallelism": f"independent problems x{args.gpus}" if args.gpus > 1 else "single GPU"}
 
@@ -340,7 +345,7 @@ def run_case(args):
     vm = V.Mesh.from_inputs(m)
     A = V.vemg_assemble(vm)
     prec = V.VEMG_PREC_FP64 if args.precision == "fp64" else V.VEMG_PREC_FP32
-    h = V.vemg_setup(A, vm, V.vemg_default_options(precision=prec))
+    h = V.vemg_setup(A, vm, V.vemg_default_options(precision=prec, precond=PRECONDS[args.precond]))
     kr = max(args.rhs, 1)
     if kr == 1:
         b = torch.from_numpy(I.normal_loads(m.n, 5)).cuda()
@@ -392,7 +397,7 @@ def main():
         t0 = time.perf_counter()
         A = V.vemg_assemble(vm)
         h = V.vemg_setup(A, vm, V.vemg_default_options(
-            precision=V.VEMG_PREC_FP64 if prec == "fp64" else V.VEMG_PREC_FP32))
+            precision=V.VEMG_PREC_FP64 if prec == "fp64" else V.VEMG_PREC_FP32, precond=PRECONDS[args.precond]))
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         r = measure(args, h, B, n, ws, rank, local, dist, V, torch, probe=not args.no_probe)

@@ -55,6 +55,11 @@ extern "C" {
 #define VEMG_NEUMANN 0
 #define VEMG_DIRICHLET_TOP 1
 
+/* preconditioner (the three compared in section 6) */
+#define VEMG_PRECOND_ADDITIVE 0  /* vertical lumping + additive smoother, Eq. ourpreconditioner (section 5.5) */
+#define VEMG_PRECOND_VL_SOR 1    /* vertical lumping as the first coarsening of a V-cycle on A with SOR smoothing */
+#define VEMG_PRECOND_SA 2        /* smoothed-aggregation AMG on A */
+
 /* precision of the preconditioner; the outer Krylov loop is always FP64 */
 #define VEMG_PREC_FP64 0   /* everything FP64, CG outer loop */
 #define VEMG_PREC_FP32 1   /* V-cycle values, vectors and arithmetic FP32, flexible CG outer loop */
@@ -91,6 +96,8 @@ typedef struct vemg_options {
     double omega_p;   /* SA prolongator smoothing weight, section 6: 2/3 */
     int coarse_max;   /* a level of at most this many rows is solved directly (dense) */
     int max_levels;   /* per multigrid chain, at most 16 */
+    int precond;      /* VEMG_PRECOND_*. With Dirichlet-top the additive form and SA are the same
+                         cycle (SA on A_bar); VL_SOR needs Neumann (VEMG_EINVAL otherwise) */
 } vemg_options;
 
 typedef struct vemg_info {
@@ -104,7 +111,7 @@ typedef struct vemg_info {
 typedef struct vemg_hierarchy vemg_hierarchy;
 
 /* Fill opts with the paper's parameters (section 6): strength 0.01, omega_p = 2/3, Neumann,
-   FP64, coarse_max = 512, max_levels = 10. */
+   FP64, coarse_max = 512, max_levels = 10, the additive preconditioner. */
 void vemg_default_options(vemg_options *opts);
 
 /* Assemble the P1 stiffness matrix A_ij = integral grad N_i . grad N_j in physical coordinates
@@ -207,7 +214,9 @@ int vemg_set_allocator(void *(*alloc)(size_t bytes, void *ctx), void (*free_fn)(
 const char *vemg_strerror(int status);
 
 /* ---- introspection and single steps (used by parity tests; all in the internal top-first
-   ordering of section 3, chain 0 = surface chain on E~^T A E~, chain 1 = A_bar chain) ---- */
+   ordering of section 3, chain 0 = surface chain on E~^T A E~, chain 1 = A_bar chain, chain 2 =
+   the single chain of VEMG_PRECOND_VL_SOR (A with E~, then the surface chain) or VEMG_PRECOND_SA)
+   ---- */
 
 /* Sizes: key is one of "n", "mtop", "nnzA", "nnzE", "nnzAc", "nlev" (of the chain), "direct"
    (coarsest level of the chain solved by the dense solve), "lev.n", "lev.nnz", "lev.nnzP",

@@ -498,11 +498,15 @@ static csr smoothed_prolongator(const csr *A, const int *agg, int nagg, double o
     double *acc = (double *)xcalloc((size_t)nagg, sizeof(double));
     for (int j = 0; j < nagg; ++j) mark[j] = -1;
     for (int i = 0; i < n; ++i) {
-        int base = P.rp[i], c = 0;
+        int base = P.rp[i], c = 0, nstrong = 0;
+        /* filtered diagonal: the dropped (weak) couplings are lumped into it, so that the
+           filtered row has the row sum of A's row and P keeps the constants A annihilates */
         double dF = d[i];
         for (int k = A->rp[i]; k < A->rp[i + 1]; ++k) {
             int j = A->ci[k];
-            if (j != i && !(fabs(A->v[k]) > theta * sqrt(d[i] * d[j]))) dF = dF - A->v[k];
+            if (j == i) continue;
+            if (fabs(A->v[k]) > theta * sqrt(d[i] * d[j])) nstrong++;
+            else dF = dF + A->v[k];
         }
         mark[agg[i]] = i; acc[agg[i]] = 0.0; P.ci[base + c++] = agg[i];
         for (int k = A->rp[i]; k < A->rp[i + 1]; ++k) {
@@ -516,7 +520,9 @@ static csr smoothed_prolongator(const csr *A, const int *agg, int nagg, double o
             acc[J] = acc[J] + a;
         }
         qsort(P.ci + base, (size_t)c, sizeof(int), cmp_int);
-        double w = omega / dF;
+        /* a row without strong couplings (or a non-positive filtered diagonal) keeps its
+           tentative row: nothing to smooth against */
+        double w = (nstrong > 0 && dF > 0.0) ? omega / dF : 0.0;
         for (int k = 0; k < c; ++k) {
             int J = P.ci[base + k];
             double t = w * acc[J];
@@ -1011,8 +1017,8 @@ void *or_setup(int n, const double *xyz, int ntet, const int *tets, const unsign
         if (rc) { or_free(h); *status = rc; return NULL; }
     } else if (h->precond == PC_VL_SOR) {
         /* level 0: A with the vertical extrapolation E~ as its prolongator; below it, the SA chain
-           of E~^T A E~ (section 6: "the vertical lumping of the equation is simply the first of a
-           multilevel multigrid cycle") */
+           of E~^T A E~ (section 6 treats the vertical lumping as the top coarsening step of one
+           multigrid cycle) */
         chain *V = &h->one, *S = &h->surf;
         memset(V, 0, sizeof(*V));
         if (S->nlev + 1 > MAX_LEVELS_CAP) { or_free(h); *status = OR_EINVAL; return NULL; }

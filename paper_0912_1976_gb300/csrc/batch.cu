@@ -515,10 +515,10 @@ __global__ void k_bcond_init(const double *g, cudaGraphConditionalHandle handle)
 template <class XT>
 static void bprecond(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
     const int K = W->K;
-    const bool neu = h->bc == VEMG_NEUMANN;
-    const int mt = neu ? h->mtop : 0;
+    const bool two = !single_chain(h);
+    const int mt = two ? h->mtop : 0;
     XT *xb = (XT *)W->lx[1][0];
-    if (neu) {
+    if (two) {
         XT *b0 = (XT *)W->lb[0][0], *x0 = (XT *)W->lx[0][0];
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_fork, s));
         VEMG_CHECK_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
@@ -796,9 +796,9 @@ BatchWork *new_batch_work(vemg_hierarchy *h, int K, cudaStream_t s) {
     VEMG_CHECK_CUDA(cudaMemsetAsync(W->Z, 0, sizeof(double) * N, s));
     const bool fp32 = h->precision == VEMG_PREC_FP32;
     size_t es = fp32 ? sizeof(float) : sizeof(double);
-    const Chain *chains[2] = {&h->surf, &h->bar};
-    if (h->bc == VEMG_NEUMANN) W->bsurf = build_bchain(h->surf, fp32, ar, s);
-    W->bbar = build_bchain(h->bar, fp32, ar, s);
+    const Chain *chains[2] = {&h->surf, single_chain(h) ? &the_chain(h) : &h->bar};
+    if (!single_chain(h)) W->bsurf = build_bchain(h->surf, fp32, ar, s);
+    W->bbar = build_bchain(*chains[1], fp32, ar, s);
     if (h->bc == VEMG_NEUMANN) {
         W->Aout = CsrP{h->A.rp, h->A.ci, h->A.v};
         W->caller_of = h->new2old;
@@ -808,7 +808,7 @@ BatchWork *new_batch_work(vemg_hierarchy *h, int K, cudaStream_t s) {
         W->caller_of = h->new2old + h->mtop;
     }
     for (int ch = 0; ch < 2; ++ch)
-        for (int l = 0; l < chains[ch]->nlev; ++l) {
+        for (int l = 0; l < chains[ch]->nlev && (ch == 1 || !single_chain(h)); ++l) {
             int64_t m = (int64_t)chains[ch]->lv[l].A.n * K;
             W->lx[ch][l] = ar.alloc<char>((int64_t)es * m);
             W->lb[ch][l] = ar.alloc<char>((int64_t)es * m);

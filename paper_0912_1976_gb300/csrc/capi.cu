@@ -94,6 +94,7 @@ static int guarded(F &&f) {
 static const Chain *chain_of(const vemg_hierarchy *h, int c) {
     if (c == 0) return &h->surf;
     if (c == 1) return &h->bar;
+    if (c == 2) return &h->one;
     return nullptr;
 }
 
@@ -111,6 +112,7 @@ void vemg_default_options(vemg_options *o) {
     o->omega_p = 2.0 / 3.0;
     o->coarse_max = 512;
     o->max_levels = 10;
+    o->precond = VEMG_PRECOND_ADDITIVE;
 }
 
 const char *vemg_strerror(int s) {
@@ -177,12 +179,14 @@ int vemg_setup(const vemg_csr *A, const vemg_mesh *mesh, const vemg_options *opt
         if ((o.bc != VEMG_NEUMANN && o.bc != VEMG_DIRICHLET_TOP) ||
             (o.precision != VEMG_PREC_FP64 && o.precision != VEMG_PREC_FP32) || !(o.strength >= 0.0) ||
             !(o.omega_p > 0.0) || o.coarse_max < 1 || o.coarse_max > 1024 || o.max_levels < 1 ||
-            o.max_levels > kMaxLevels)
+            o.max_levels > kMaxLevels || o.precond < VEMG_PRECOND_ADDITIVE || o.precond > VEMG_PRECOND_SA ||
+            (o.precond == VEMG_PRECOND_VL_SOR && o.bc != VEMG_NEUMANN))
             return VEMG_EINVAL;
         h = new vemg_hierarchy();
         h->opts = o;
         h->bc = o.bc;
         h->precision = o.precision;
+        h->precond = o.bc == VEMG_DIRICHLET_TOP ? VEMG_PRECOND_ADDITIVE : o.precond;
         setup(h, A, mesh, (cudaStream_t)stream);
         prepare_solve(h, (cudaStream_t)stream);
         return VEMG_OK;

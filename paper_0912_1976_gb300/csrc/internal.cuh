@@ -184,6 +184,8 @@ struct vemg_hierarchy {
     double *bary = nullptr;
     vemg::DCsr E, ET, Ac;
     vemg::Chain surf, bar;
+    vemg::Chain one;                             // the single chain of VL_SOR / SA
+    int precond = VEMG_PRECOND_ADDITIVE;
     // Krylov work vectors (internal order, length n)
     double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *b = nullptr;
     float *rf = nullptr, *zf = nullptr;           // mixed precision preconditioner input / output
@@ -213,6 +215,12 @@ struct vemg_hierarchy {
 };
 
 namespace vemg {
+// the preconditioner is one V-cycle of one chain (Dirichlet-top, VL_SOR, SA) rather than the two
+// branches of the additive form
+inline bool single_chain(const vemg_hierarchy *h) {
+    return h->bc == VEMG_DIRICHLET_TOP || h->precond != VEMG_PRECOND_ADDITIVE;
+}
+inline const Chain &the_chain(const vemg_hierarchy *h) { return h->bc == VEMG_DIRICHLET_TOP ? h->bar : h->one; }
 // setup.cu
 void assemble(const vemg_mesh *mesh, vemg_csr *A_out, cudaStream_t s);
 void load_vector(const vemg_mesh *mesh, const double *f, double *b, cudaStream_t s);

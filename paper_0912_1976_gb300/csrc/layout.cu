@@ -225,9 +225,9 @@ __global__ void k_compose(int n, const int *__restrict__ a, const int *__restric
 void build_solve_layout(vemg_hierarchy *h, cudaStream_t s) {
     Arena &ar = h->arena;
     bool fp32 = h->precision == VEMG_PREC_FP32;
-    layout_chain(ar, h->bar, h->sbar, fp32, s);
     int n = h->n, mt = h->mtop;
-    if (h->bc == VEMG_NEUMANN) {
+    if (!single_chain(h)) {
+        layout_chain(ar, h->bar, h->sbar, fp32, s);
         layout_chain(ar, h->surf, h->ssurf, fp32, s);
         h->nu = n;
         Scratch<int> s2n(n), n2s(n);
@@ -246,15 +246,20 @@ void build_solve_layout(vemg_hierarchy *h, cudaStream_t s) {
         k_compose<<<grid_for(n, 256), 256, 0, s>>>(n, h->new2old, s2n, 0, h->caller_of);
         VEMG_CHECK_LAUNCH();
     } else {
-        int nb = n - mt;
+        // one chain whose level 0 is the operator of the unknowns (A_bar for Dirichlet-top, A for
+        // the VL_SOR / SA preconditioners); the outer vectors use its level-0 colour order
+        const Chain &C = the_chain(h);
+        layout_chain(ar, C, h->sbar, fp32, s);
+        int off = h->bc == VEMG_DIRICHLET_TOP ? mt : 0;
+        int nb = n - off;
         h->nu = nb;
-        const Level &L0 = h->bar.lv[0];
+        const Level &L0 = C.lv[0];
         Scratch<int> inv(nb);
         k_inverse_perm<<<grid_for(nb, 256), 256, 0, s>>>(nb, L0.crow, inv);
         VEMG_CHECK_LAUNCH();
         h->Aop = build_sell(ar, L0.A, nb, L0.crow, inv, nb, {0, nb}, false, false, nullptr, nullptr, nullptr, s);
         h->caller_of = ar.alloc<int>(nb);
-        k_compose<<<grid_for(nb, 256), 256, 0, s>>>(nb, h->new2old + mt, L0.crow, 0, h->caller_of);
+        k_compose<<<grid_for(nb, 256), 256, 0, s>>>(nb, h->new2old + off, L0.crow, 0, h->caller_of);
         VEMG_CHECK_LAUNCH();
     }
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));

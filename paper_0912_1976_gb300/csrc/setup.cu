@@ -1030,7 +1030,9 @@ static int sa_aggregate(Arena &ar, const DCsr &A, const double *d, double theta,
 }
 
 // smoothed prolongator P = (I - omega (D^F)^-1 A^F) P_tent with Vanek's filtered matrix:
-// weak off-diagonal entries dropped and added to the diagonal (section 6: omega = 2/3)
+// weak off-diagonal entries dropped and lumped into the diagonal, so that each filtered row keeps
+// the row sum of A and P keeps the constants (section 6: omega = 2/3). A row with no strong
+// coupling, or a non-positive filtered diagonal, keeps its tentative row.
 __global__ void k_prolong_len(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                               const double *__restrict__ v, const double *__restrict__ d, double theta,
                               const int *__restrict__ agg, int *len, int *err) {
@@ -1059,11 +1061,16 @@ __global__ void k_prolong_fill(int n, const int *__restrict__ rp, const int *__r
     int *u = pci + lo;
     c = insert_unique(u, c, hi - lo, agg[i]);
     double dF = d[i];
+    int nstrong = 0;
     for (int k = rp[i]; k < rp[i + 1]; ++k) {
         int j = ci[k];
         if (j == i) continue;
-        if (strong(v[k], d[i], d[j], theta)) c = insert_unique(u, c, hi - lo, agg[j]);
-        else dF = dF - v[k];
+        if (strong(v[k], d[i], d[j], theta)) {
+            c = insert_unique(u, c, hi - lo, agg[j]);
+            nstrong++;
+        } else {
+            dF = dF + v[k];
+        }
     }
     for (int k = lo; k < hi; ++k) pv[k] = 0.0;
     for (int k = rp[i]; k < rp[i + 1]; ++k) {
@@ -1075,7 +1082,7 @@ __global__ void k_prolong_fill(int n, const int *__restrict__ rp, const int *__r
         int pos = bsearch_row(pci, lo, hi, agg[j]);
         pv[pos] = pv[pos] + a;
     }
-    double w = omega / dF;
+    double w = (nstrong > 0 && dF > 0.0) ? omega / dF : 0.0;
     int ai = agg[i];
     for (int k = lo; k < hi; ++k) {
         double t = w * pv[k];
@@ -1476,6 +1483,32 @@ void setup(vemg_hierarchy *h, const vemg_csr *Ain, const vemg_mesh *mesh, cudaSt
     }
     h->bar.is_bar = true;
     build_chain(ar, h->bar, Abar, false, h->opts, s);
+    if (h->bc == VEMG_NEUMANN && h->precond == VEMG_PRECOND_SA) {
+        build_chain(ar, h->one, copy_csr(ar, h->A, s), true, h->opts, s);
+    } else if (h->bc == VEMG_NEUMANN && h->precond == VEMG_PRECOND_VL_SOR) {
+        // level 0: A with the vertical extrapolation E~ as its prolongator; below it the SA chain of
+        // E~^T A E~ (section 6: the vertical lumping is the first coarsening of the cycle)
+        Chain &V = h->one;
+        const Chain &S = h->surf;
+        if (S.nlev + 1 > kMaxLevels) throw Error{VEMG_EINVAL};
+        V.singular = true;
+        V.nlev = S.nlev + 1;
+        V.lv[0].A = h->A;
+        V.lv[0].P = h->E;
+        V.lv[0].PT = h->ET;
+        for (int l = 0; l < S.nlev; ++l) V.lv[l + 1] = S.lv[l];
+        V.direct = S.direct;
+        V.nc = S.nc;
+        V.G = S.G;
+        Level &L = V.lv[0];
+        colour_level(ar, L, s);
+        L.diag = ar.alloc<double>(L.A.n);
+        k_diag<<<grid_for(L.A.n, 256), 256, 0, s>>>(L.A.n, L.A.rp, L.A.ci, L.A.v, L.diag);
+        VEMG_CHECK_LAUNCH();
+        L.x = ar.alloc<double>(L.A.n);
+        L.b = ar.alloc<double>(L.A.n);
+        L.r = ar.alloc<double>(L.A.n);
+    }
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -550,9 +550,10 @@ template <class XT>
 static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, cudaStream_t s) {
     const SChain &B = h->sbar;
     const bool neu = h->bc == VEMG_NEUMANN, flex = h->precision != VEMG_PREC_FP64;
-    const int mt = neu ? h->mtop : 0;
+    const bool two = !single_chain(h);
+    const int mt = two ? h->mtop : 0;
     const XT *ys = nullptr;
-    if (neu) {
+    if (two) {
         const SChain &S = h->ssurf;
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_fork, s));
         VEMG_CHECK_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
@@ -564,7 +565,7 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
     }
     // additive smoother: one V-cycle on A_bar with the trailing part of r
     vcycle_level<XT, double>(B, 0, r + mt, (XT *)B.lv[0].x, s);
-    if (neu) VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+    if (two) VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
     k_combine<XT><<<kRedBlocks, kRedThreads, 0, s>>>(h->nu, mt, sargs(h->Enon), ys, (const XT *)B.lv[0].x, z, r,
                                                      h->q, neu, flex, first, 1.0 / (double)h->nu, h->scal,
                                                      h->red + 5 * kRedBlocks * C_Z, h->ctr + C_Z);
@@ -899,9 +900,12 @@ void vcycle(vemg_hierarchy *h, int chain, const double *b, double *x, cudaStream
     prepare_solve(h, s);
     g_probe = &h->probe;
     g_count = &h->launches;
-    const Chain &C = chain == 0 ? h->surf : h->bar;
+    const Chain &C = chain == 0 ? h->surf : chain == 2 ? h->one : h->bar;
+    // the solve layout holds the chain the preconditioner uses: surface and A_bar chains of the
+    // additive form, or the single chain
+    bool have = single_chain(h) ? (chain == 2 || (chain == 1 && h->bc == VEMG_DIRICHLET_TOP)) : chain != 2;
+    if (C.nlev == 0 || !have) throw Error{VEMG_EINVAL};
     const SChain &S = chain == 0 ? h->ssurf : h->sbar;
-    if (C.nlev == 0) throw Error{VEMG_EINVAL};
     int n = C.lv[0].A.n;
     bool f = S.fp32;
     Scratch<char> bs((int64_t)n * 8), xs((int64_t)n * 8);

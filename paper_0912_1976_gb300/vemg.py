@@ -18,6 +18,7 @@ VEMG_OK, VEMG_EINVAL, VEMG_EMESH, VEMG_ENOMEM, VEMG_ENOTCONV, VEMG_EBREAKDOWN, V
     VEMG_EINTERNAL = range(9)
 VEMG_NEUMANN, VEMG_DIRICHLET_TOP = 0, 1
 VEMG_PREC_FP64, VEMG_PREC_FP32 = 0, 1
+VEMG_PRECOND_ADDITIVE, VEMG_PRECOND_VL_SOR, VEMG_PRECOND_SA = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ENOTCONV", 5: "EBREAKDOWN",
                 6: "ETIMEOUT", 7: "ECUDA", 8: "EINTERNAL"}
 
@@ -35,7 +36,7 @@ class vemg_csr(C.Structure):
 
 class vemg_options(C.Structure):
     _fields_ = [("bc", C.c_int), ("precision", C.c_int), ("strength", C.c_double), ("omega_p", C.c_double),
-                ("coarse_max", C.c_int), ("max_levels", C.c_int)]
+                ("coarse_max", C.c_int), ("max_levels", C.c_int), ("precond", C.c_int)]
 
 
 class vemg_info(C.Structure):

@@ -431,3 +431,78 @@ def test_iterations_independent_of_aspect_ratio():
         jac.append(_jacobi_pcg_iters(P.csr("A"), bi - bi.mean(), 1e-8))
     assert max(its) <= 1.25 * min(its), its
     assert jac[0] < jac[1] < jac[2] and jac[2] > 2 * jac[0], jac
+
+
+# --------------------------------------------------------------------------------------------
+# the two other preconditioners of section 6: vertical lumping as the first coarsening of a
+# V-cycle on A with SOR smoothing (VL+SOR), and smoothed aggregation on A itself (SA)
+
+@pytest.mark.parametrize("pc", [O.PC_VL_SOR, O.PC_SA])
+def test_variant_cycles_symmetric_positive(pc):
+    """Forward SOR before and backward SOR after the coarse correction, with P^T restriction, make
+    the cycle a symmetric operator, positive semi-definite with the constants as kernel."""
+    m = _mesh(5, 3, h0=0.01, zj=0.3)
+    P = O.Problem(m, coarse_max=40, precond=pc)
+    n = P.n
+    Mz = np.stack([P.precond(e) for e in np.eye(n)], axis=1)
+    assert np.abs(Mz - Mz.T).max() <= 1e-10 * np.abs(Mz).max()
+    w = np.linalg.eigvalsh(0.5 * (Mz + Mz.T))
+    assert w[0] > -1e-10 * w[-1]
+    assert P.nlev(2) >= 2
+
+
+def test_vl_chain_is_extrapolation_then_surface_sa():
+    """VL+SOR: the finest level is A with E~ as its prolongator; the level below is the Galerkin
+    product E~^T A E~ written out here with scipy, then the SA levels of that operator."""
+    m = _mesh(10, 4, h0=1e-3, zj=0.3)
+    P = O.Problem(m, precond=O.PC_VL_SOR)
+    A, E = P.csr("A"), P.csr("E")
+    assert np.array_equal(P.csr("lev.A", 2, 0).toarray(), A.toarray())
+    assert np.array_equal(P.csr("lev.P", 2, 0).toarray(), E.toarray())
+    Ac = P.csr("lev.A", 2, 1).toarray()
+    ref = (E.T @ (A @ E)).toarray()
+    assert np.abs(Ac - ref).max() <= 1e-12 * np.abs(ref).max()
+    Padd = O.Problem(m)
+    assert P.nlev(2) == Padd.nlev(0) + 1
+    for l in range(Padd.nlev(0)):
+        assert np.array_equal(P.csr("lev.A", 2, l + 1).toarray(), Padd.csr("lev.A", 0, l).toarray())
+    # the finest-level colouring is a proper colouring of A's graph
+    col = P.ints("lev.colour", 2, 0)
+    Ac0 = A.tocoo()
+    off = Ac0.row != Ac0.col
+    assert not np.any(col[Ac0.row[off]] == col[Ac0.col[off]])
+
+
+def test_sa_chain_galerkin_and_constants():
+    m = _mesh(10, 4, h0=1e-2, zj=0.3)
+    P = O.Problem(m, precond=O.PC_SA)
+    assert np.array_equal(P.csr("lev.A", 2, 0).toarray(), P.csr("A").toarray())
+    for l in range(P.nlev(2) - 1):
+        A, Pl, Ac = P.csr("lev.A", 2, l), P.csr("lev.P", 2, l), P.csr("lev.A", 2, l + 1)
+        ref = (Pl.T @ (A @ Pl)).toarray()
+        assert np.abs(Ac.toarray() - ref).max() <= 1e-12 * np.abs(ref).max()
+        assert np.abs(Pl @ np.ones(Pl.shape[1]) - 1).max() <= 1e-9
+
+
+def test_vl_sor_rejected_with_dirichlet_top():
+    m = _mesh(5, 3)
+    with pytest.raises(Exception):
+        O.Problem(m, bc=O.BC_DIRICHLET_TOP, precond=O.PC_VL_SOR)
+
+
+def test_section6_sa_degrades_with_aspect_ratio_vl_does_not():
+    """Section 6 (genuinely unstructured meshes): plain SA needs ever more iterations as the
+    aspect ratio shrinks, while both forms built on vertical lumping stay nearly constant."""
+    its = {pc: [] for pc in (O.PC_ADDITIVE, O.PC_VL_SOR, O.PC_SA)}
+    for eps in [1e-1, 1e-2, 1e-4]:
+        m = I.make_mesh(12, 12, 6, I.depth_sines(eps), z_jitter=0.3, xy_jitter=0.2, seed=8)
+        for pc in its:
+            P = O.Problem(m, precond=pc)
+            r = P.solve(I.normal_loads(P.n, 2), tol=1e-7, maxit=2000)
+            assert r["status"] == "OK"
+            its[pc].append(r["iters"])
+    for pc in (O.PC_ADDITIVE, O.PC_VL_SOR):
+        assert max(its[pc]) <= 1.3 * min(its[pc]), its
+    assert its[O.PC_SA][-1] > 5 * its[O.PC_SA][0], its
+    # the multiplicative VL+SOR cycle needs fewer iterations than the additive one
+    assert all(v < a for v, a in zip(its[O.PC_VL_SOR], its[O.PC_ADDITIVE])), its
