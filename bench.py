@@ -35,6 +35,7 @@ METRIC = "solves/s at FP64 rel-res 1e-8"
 
 
 PRECONDS = {"additive": 0, "vl_sor": 1, "sa": 2}
+CYCLES = {"persistent": 0, "launches": 1}
 
 
 def parse():
@@ -44,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vemg", choices=["vemg", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--cycle", default="persistent", choices=["persistent", "launches"],
+                    help="one cooperative kernel per preconditioner application, or one kernel per phase")
     ap.add_argument("--precond", default="additive", choices=list(PRECONDS),
                     help="additive (the paper's preconditioner), vl_sor or sa (its two comparison forms)")
     ap.add_argument("--workload", default=WORKLOAD)
@@ -54,6 +57,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (0: 0.8 x saturation)")
     ap.add_argument("--case", default="",
                     help="profiling case NXxNYxNZ (z-jitter 0.3, eps 1e-3): two untimed solves, then exit")
+    ap.add_argument("--stream-path", action="store_true",
+                    help="with --case: launch the solve's kernels on the stream, not from CUDA graphs")
     ap.add_argument("--rhs", type=int, default=0,
                     help="right-hand sides per step (0: the workload's own count); >1 uses vemg_solve_batch")
     return ap.parse_args()
@@ -121,6 +126,32 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms, dist, torch):
+    """The slowest rank's time: every rank runs its own problems (weak scaling), so the job ends
+    when the last one does. NCCL reduces a device tensor, gloo a host one."""
+    if not dist:
+        return ms
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, dist, torch):
+    if not dist:
+        return v
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_rate(ws, units_per_rank_step, steps, ms):
+    """Units per second of the whole job: every rank processed units_per_rank_step units in each
+    of `steps` steps, and the job took ms milliseconds (the max over ranks)."""
+    return ws * units_per_rank_step * steps / (ms / 1000.0)
+
+
 # --------------------------------------------------------------------------------------------
 # the CPU oracle: the reference arm and the cpu_baseline leg
 
@@ -186,7 +217,7 @@ def workload_config(args, n):
     return {"workload": f"{args.workload}: {w['nx']}x{w['ny']}x{w['nz']} extruded hex->6 tets, {n} nodes, "
                         f"H0 {w['depth'][1]:g}, z-jitter {w['z_jitter']}, xy-jitter {w['xy_jitter']}, "
                         f"all-Neumann, N(0,1) loads mean-zero, rtol {RTOL:g}",
-            "precision": args.precision, "preconditioner": args.precond, "rhs_per_step": kr,
+            "precision": args.precision, "preconditioner": args.precond, "cycle": args.cycle, "rhs_per_step": kr,
             "l2": "inputs larger than L2 (A alone 0.39 GB; no flush needed)",
             "parallelism": f"independent problems x{args.gpus}" if args.gpus > 1 else "single GPU"}
 
@@ -233,14 +264,11 @@ def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe):
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
     launches = V.vemg_kernel_launches(h) - l0
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, torch)
     iters = [i["iters"] for i in infos]
-    out = {"value": ws * kcols * args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps, "iters": iters,
+    out = {"value": whole_job_rate(ws, kcols, args.steps, ms), "ms_per_step": ms / args.steps, "iters": iters,
            "true_relres_max": max(i["true_relres"] for i in infos),
-           "gdof_iter_per_s": ws * kcols * sum(n * it for it in iters) / (ms / 1000.0) / 1e9,
+           "gdof_iter_per_s": sum_over_ranks(kcols * sum(n * it for it in iters), dist, torch) / (ms / 1000.0) / 1e9,
            "gpu_launches": launches, "clocks": clocks}
     # end to end: host buffers, host-to-device copy of the step's inputs and device-to-host copy
     # of its results inside the timed region (vemg_solve_host for one right-hand side; pinned
@@ -270,16 +298,18 @@ def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe):
     e1.record()
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    out["e2e"] = {"value": ws * kcols * args.steps / (ms_e2e / 1000.0), "unit": "solves/s",
+    ms_e2e = max_over_ranks(ms_e2e, dist, torch)
+    out["e2e"] = {"value": whole_job_rate(ws, kcols, args.steps, ms_e2e), "unit": "solves/s",
                   "h2d_bytes_per_step": 8 * n * kcols, "d2h_bytes_per_step": 8 * n * kcols}
     classes = {}
     if probe and not batched:
-        kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "sor_fine": V.VEMG_PROBE_SOR_FINE, "sor_all": V.VEMG_PROBE_SOR,
-                 "residual": V.VEMG_PROBE_RESIDUAL}
+        # the persistent cycle (one kernel per preconditioner application) or, with per-phase
+        # launches, its kernel classes
+        if args.cycle == "persistent":
+            kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "vcycle": V.VEMG_PROBE_VCYCLE}
+        else:
+            kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "sor_fine": V.VEMG_PROBE_SOR_FINE, "sor_all": V.VEMG_PROBE_SOR,
+                     "residual": V.VEMG_PROBE_RESIDUAL}
         for name, kind in kinds.items():
             V.vemg_probe(h, kind)
             for j in range(2):
@@ -345,8 +375,13 @@ def run_case(args):
     vm = V.Mesh.from_inputs(m)
     A = V.vemg_assemble(vm)
     prec = V.VEMG_PREC_FP64 if args.precision == "fp64" else V.VEMG_PREC_FP32
-    h = V.vemg_setup(A, vm, V.vemg_default_options(precision=prec, precond=PRECONDS[args.precond]))
+    h = V.vemg_setup(A, vm, V.vemg_default_options(precision=prec, precond=PRECONDS[args.precond],
+                                                   cycle=CYCLES[args.cycle]))
     kr = max(args.rhs, 1)
+    if args.stream_path:
+        # the same kernels launched on the stream instead of from graphs (profilers cannot see
+        # into graphs with conditional nodes)
+        V.vemg_probe(h, V.VEMG_PROBE_VCYCLE)
     if kr == 1:
         b = torch.from_numpy(I.normal_loads(m.n, 5)).cuda()
         for _ in range(2):
@@ -397,7 +432,8 @@ def main():
         t0 = time.perf_counter()
         A = V.vemg_assemble(vm)
         h = V.vemg_setup(A, vm, V.vemg_default_options(
-            precision=V.VEMG_PREC_FP64 if prec == "fp64" else V.VEMG_PREC_FP32, precond=PRECONDS[args.precond]))
+            precision=V.VEMG_PREC_FP64 if prec == "fp64" else V.VEMG_PREC_FP32, precond=PRECONDS[args.precond],
+            cycle=CYCLES[args.cycle]))
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         r = measure(args, h, B, n, ws, rank, local, dist, V, torch, probe=not args.no_probe)

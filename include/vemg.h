@@ -60,6 +60,10 @@ extern "C" {
 #define VEMG_PRECOND_VL_SOR 1    /* vertical lumping as the first coarsening of a V-cycle on A with SOR smoothing */
 #define VEMG_PRECOND_SA 2        /* smoothed-aggregation AMG on A */
 
+/* how a preconditioner application is launched */
+#define VEMG_CYCLE_PERSISTENT 0  /* one cooperative kernel runs every phase of the V-cycles */
+#define VEMG_CYCLE_LAUNCHES 1    /* one kernel per phase (colour sweep, residual, transfer) */
+
 /* precision of the preconditioner; the outer Krylov loop is always FP64 */
 #define VEMG_PREC_FP64 0   /* everything FP64, CG outer loop */
 #define VEMG_PREC_FP32 1   /* V-cycle values, vectors and arithmetic FP32, flexible CG outer loop */
@@ -98,6 +102,7 @@ typedef struct vemg_options {
     int max_levels;   /* per multigrid chain, at most 16 */
     int precond;      /* VEMG_PRECOND_*. With Dirichlet-top the additive form and SA are the same
                          cycle (SA on A_bar); VL_SOR needs Neumann (VEMG_EINVAL otherwise) */
+    int cycle;        /* VEMG_CYCLE_*: same arithmetic, different launch structure */
 } vemg_options;
 
 typedef struct vemg_info {
@@ -111,7 +116,7 @@ typedef struct vemg_info {
 typedef struct vemg_hierarchy vemg_hierarchy;
 
 /* Fill opts with the paper's parameters (section 6): strength 0.01, omega_p = 2/3, Neumann,
-   FP64, coarse_max = 512, max_levels = 10, the additive preconditioner. */
+   FP64, coarse_max = 512, max_levels = 10, the additive preconditioner, persistent cycles. */
 void vemg_default_options(vemg_options *opts);
 
 /* Assemble the P1 stiffness matrix A_ij = integral grad N_i . grad N_j in physical coordinates
@@ -213,6 +218,19 @@ int vemg_set_allocator(void *(*alloc)(size_t bytes, void *ctx), void (*free_fn)(
 /* Human-readable name of a status code (static string). */
 const char *vemg_strerror(int status);
 
+/* The CUDA error behind the last VEMG_ECUDA returned on this host thread: the runtime's message,
+   the failing call and its source location. Empty if none. The string is owned by the library
+   and stays valid until the next failing call on this thread. */
+const char *vemg_last_error(void);
+
+/* Self-test of the bounded wait behind VEMG_CYCLE_PERSISTENT (no counterpart in the paper): a
+   cooperative launch of launched_blocks CTAs meets at one grid barrier that expects
+   claimed_blocks CTAs (1 <= launched_blocks <= claimed_blocks <= 8, else VEMG_EINVAL). Equal
+   counts: the barrier completes, VEMG_OK. claimed > launched: it can never complete, every wait
+   gives up after a few milliseconds and the call returns VEMG_ETIMEOUT with the CUDA context
+   intact. Allocates 12 bytes of device memory; synchronous on the stream. */
+int vemg_selftest_barrier(int claimed_blocks, int launched_blocks, void *stream);
+
 /* ---- introspection and single steps (used by parity tests; all in the internal top-first
    ordering of section 3, chain 0 = surface chain on E~^T A E~, chain 1 = A_bar chain, chain 2 =
    the single chain of VEMG_PRECOND_VL_SOR (A with E~, then the surface chain) or VEMG_PRECOND_SA)
@@ -267,6 +285,7 @@ int vemg_kernel_launches(const vemg_hierarchy *h, int64_t *count);
 #define VEMG_PROBE_SOR 2         /* every multicolour SOR launch of both chains */
 #define VEMG_PROBE_RESIDUAL 3    /* every V-cycle residual launch */
 #define VEMG_PROBE_SOR_FINE 4    /* SOR launches on the finest level of the A_bar chain */
+#define VEMG_PROBE_VCYCLE 5      /* the persistent preconditioner kernel (VEMG_CYCLE_PERSISTENT) */
 
 /* Start timing one kernel class (VEMG_PROBE_NONE stops): every later launch of that class
    records a CUDA event before and after itself on its stream. Resets the accumulated totals. */
@@ -276,6 +295,18 @@ int vemg_probe(vemg_hierarchy *h, int kind);
    milliseconds, number of launches, and summed algorithmic bytes, i.e. for a sparse pass
    nnz (value + index bytes) + rows (row pointer + vector reads and writes). */
 int vemg_probe_read(vemg_hierarchy *h, double *total_ms, int64_t *launches, double *algorithmic_bytes);
+
+/* Per-phase profile of the persistent preconditioner kernel, summed over the applications run
+   since vemg_probe(h, VEMG_PROBE_VCYCLE): for phase k of the program, its kind op[k] (0 one SOR
+   colour, 1 residual, 2 y = S x (restriction or E~ transfer), 3 y += S x (prolongation), 4 E~^T r
+   of the outer residual, 5 dense coarsest solve), its multigrid level, its CTA group (0 surface,
+   1 A_bar; a single chain has group 0 only) and the SM clock cycles from the end of the previous
+   phase's barrier to the end of its own, seen by the group's first CTA (the phase's critical
+   path). capacity: entries the caller's arrays hold; *count receives the number of phases
+   (VEMG_EINVAL, with *count set, if capacity is smaller; 0 phases without a persistent program).
+   Synchronises the device. */
+int vemg_probe_phases(vemg_hierarchy *h, int capacity, int *count, int *op, int *level, int *group,
+                      double *cycles);
 
 #ifdef __cplusplus
 }

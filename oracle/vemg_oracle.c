@@ -469,7 +469,8 @@ int or_colour(int n, const int *rp, const int *ci, int *colour) {
 
 /* smoothed prolongator P = (I - omega (D^F)^-1 A^F) P_tent (section 6: omega = 2/3), with the
    filtered matrix of Vanek, Mandel and Brezina (1996): weak off-diagonal entries are dropped and
-   added to the diagonal, A^F_ii = A_ii - sum_{j weak} A_ij, so that A^F 1 = A 1. Sums run over
+   lumped into the diagonal, A^F_ii = A_ii + sum_{j weak} A_ij, so that A^F 1 = A 1. A row with no
+   strong coupling (or a non-positive filtered diagonal) keeps its tentative row. Sums run over
    the row in ascending column order. */
 static csr smoothed_prolongator(const csr *A, const int *agg, int nagg, double omega, double theta) {
     int n = A->n;

@@ -24,6 +24,7 @@ UNITS = {
     "batch.cu": [],
     "capi.cu": [],
     "noalloc.cu": [],
+    "persist.cu": [],
 }
 
 

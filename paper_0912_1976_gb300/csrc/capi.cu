@@ -113,6 +113,13 @@ void vemg_default_options(vemg_options *o) {
     o->coarse_max = 512;
     o->max_levels = 10;
     o->precond = VEMG_PRECOND_ADDITIVE;
+    o->cycle = VEMG_CYCLE_PERSISTENT;
+}
+
+const char *vemg_last_error(void) { return last_cuda_error(); }
+
+int vemg_selftest_barrier(int claimed_blocks, int launched_blocks, void *stream) {
+    return guarded([&] { return barrier_selftest(claimed_blocks, launched_blocks, (cudaStream_t)stream); });
 }
 
 const char *vemg_strerror(int s) {
@@ -180,7 +187,8 @@ int vemg_setup(const vemg_csr *A, const vemg_mesh *mesh, const vemg_options *opt
             (o.precision != VEMG_PREC_FP64 && o.precision != VEMG_PREC_FP32) || !(o.strength >= 0.0) ||
             !(o.omega_p > 0.0) || o.coarse_max < 1 || o.coarse_max > 1024 || o.max_levels < 1 ||
             o.max_levels > kMaxLevels || o.precond < VEMG_PRECOND_ADDITIVE || o.precond > VEMG_PRECOND_SA ||
-            (o.precond == VEMG_PRECOND_VL_SOR && o.bc != VEMG_NEUMANN))
+            (o.precond == VEMG_PRECOND_VL_SOR && o.bc != VEMG_NEUMANN) ||
+            (o.cycle != VEMG_CYCLE_PERSISTENT && o.cycle != VEMG_CYCLE_LAUNCHES))
             return VEMG_EINVAL;
         h = new vemg_hierarchy();
         h->opts = o;
@@ -210,6 +218,7 @@ void vemg_destroy(vemg_hierarchy *h) {
     cudaDeviceSynchronize();
     release_graphs(h);
     release_batch(h);
+    release_persist(h);
     for (auto &e : h->probe.ev) cudaEventDestroy(e);
     h->arena.release();
     delete h;
@@ -339,7 +348,7 @@ int vemg_precond(vemg_hierarchy *h, const double *r, double *z, void *stream) {
 
 int vemg_vcycle(vemg_hierarchy *h, int chain, const double *b, double *x, void *stream) {
     return guarded([&] {
-        if (!h || !b || !x || (chain != 0 && chain != 1)) return VEMG_EINVAL;
+        if (!h || !b || !x || chain < 0 || chain > 2) return VEMG_EINVAL;
         vcycle(h, chain, b, x, (cudaStream_t)stream);
         VEMG_CHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
         return VEMG_OK;
@@ -354,9 +363,19 @@ int vemg_kernel_launches(const vemg_hierarchy *h, int64_t *count) {
 
 int vemg_probe(vemg_hierarchy *h, int kind) {
     return guarded([&] {
-        if (!h || kind < VEMG_PROBE_NONE || kind > VEMG_PROBE_SOR_FINE) return VEMG_EINVAL;
+        if (!h || kind < VEMG_PROBE_NONE || kind > VEMG_PROBE_VCYCLE) return VEMG_EINVAL;
         probe_start(h, kind);
+        if (kind == VEMG_PROBE_VCYCLE) persist_profile_reset(h);
         return VEMG_OK;
+    });
+}
+
+int vemg_probe_phases(vemg_hierarchy *h, int capacity, int *count, int *op, int *level, int *group,
+                      double *cycles) {
+    return guarded([&] {
+        if (!h || !count || capacity < 0 || (capacity > 0 && (!op || !level || !group || !cycles)))
+            return VEMG_EINVAL;
+        return persist_profile(h, capacity, count, op, level, group, cycles);
     });
 }
 

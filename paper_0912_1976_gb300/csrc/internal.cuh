@@ -109,7 +109,9 @@ struct Level {
 
 // Opt-in timing of one kernel class: CUDA events recorded on the launching stream around each
 // launch, plus the algorithmic bytes of each launch (bytes the operation must move at minimum).
-enum ProbeKind { PROBE_NONE = 0, PROBE_SPMV_A = 1, PROBE_SOR = 2, PROBE_RESIDUAL = 3, PROBE_SOR_FINE = 4 };
+enum ProbeKind {
+    PROBE_NONE = 0, PROBE_SPMV_A = 1, PROBE_SOR = 2, PROBE_RESIDUAL = 3, PROBE_SOR_FINE = 4, PROBE_VCYCLE = 5
+};
 
 struct Probe {
     int kind = PROBE_NONE;
@@ -171,6 +173,7 @@ struct Chain {
 
 struct Graphs;
 struct BatchWork;
+struct Persist;
 
 }  // namespace vemg
 
@@ -212,6 +215,7 @@ struct vemg_hierarchy {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     unsigned *ctr = nullptr;                      // arrival counters of the block reductions
     vemg::BatchWork *batch = nullptr;             // multi-right-hand-side work (batch.cu)
+    vemg::Persist *persist = nullptr;             // the persistent preconditioner program (persist.cu)
 };
 
 namespace vemg {
@@ -221,6 +225,16 @@ inline bool single_chain(const vemg_hierarchy *h) {
     return h->bc == VEMG_DIRICHLET_TOP || h->precond != VEMG_PRECOND_ADDITIVE;
 }
 inline const Chain &the_chain(const vemg_hierarchy *h) { return h->bc == VEMG_DIRICHLET_TOP ? h->bar : h->one; }
+// persist.cu
+void build_persist(vemg_hierarchy *h, cudaStream_t s);
+void release_persist(vemg_hierarchy *h);
+void launch_persist(vemg_hierarchy *h, const double *r, cudaStream_t s);
+void persist_reset(vemg_hierarchy *h, cudaStream_t s);
+double persist_bytes(const vemg_hierarchy *h);
+const int *persist_err(const vemg_hierarchy *h);
+int barrier_selftest(int claimed, int launched, cudaStream_t s);
+void persist_profile_reset(vemg_hierarchy *h);
+int persist_profile(vemg_hierarchy *h, int cap, int *count, int *op, int *level, int *group, double *cycles);
 // setup.cu
 void assemble(const vemg_mesh *mesh, vemg_csr *A_out, cudaStream_t s);
 void load_vector(const vemg_mesh *mesh, const double *f, double *b, cudaStream_t s);

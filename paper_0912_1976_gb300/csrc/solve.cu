@@ -42,8 +42,9 @@ static constexpr int kProbePairs = 1024;
 
 static void probe_flush(Probe &p) {
     if (p.used == 0) return;
-    VEMG_CHECK_CUDA(cudaEventSynchronize(p.ev[2 * p.used - 1]));
     for (int i = 0; i < p.used; ++i) {
+        // the pairs may sit on two streams (surface and A_bar branches): wait for each one
+        VEMG_CHECK_CUDA(cudaEventSynchronize(p.ev[2 * i + 1]));
         float ms = 0.f;
         VEMG_CHECK_CUDA(cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]));
         p.total_ms += ms;
@@ -394,7 +395,8 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(int nu, int mtop, SellA
                                                          const XT *__restrict__ xb, double *__restrict__ z,
                                                          const double *__restrict__ r, const double *__restrict__ q,
                                                          int neumann, int flexible, int first, double inv_n,
-                                                         double *sc, double *part, unsigned *ctr) {
+                                                         double *sc, double *part, unsigned *ctr,
+                                                         const int *__restrict__ perr) {
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     constexpr int stride = kRedBlocks * kRedThreads;
     const bool dots_q = flexible && !first;
@@ -458,6 +460,7 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(int nu, int mtop, SellA
     sc[S_BETA] = beta;
     sc[S_RZ] = rz;
     if (!(rz == rz) || !(beta == beta)) sc[S_FLAG] = 1.0;
+    if (perr && *(const volatile int *)perr) sc[S_FLAG] = 2.0;   // the persistent cycle gave up waiting
 }
 
 // p = (z - mu) + beta p
@@ -553,7 +556,18 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
     const bool two = !single_chain(h);
     const int mt = two ? h->mtop : 0;
     const XT *ys = nullptr;
-    if (two) {
+    // probes of the per-phase kernel classes time the launch-per-phase cycle
+    const int pk = h->probe.kind;
+    const bool persist = h->persist && pk != PROBE_SOR && pk != PROBE_SOR_FINE && pk != PROBE_RESIDUAL;
+    if (persist) {
+        // both branches (or the single chain) in one cooperative kernel
+        {
+            ProbeScope ps(PROBE_VCYCLE, persist_bytes(h), s);
+            launch_persist(h, r, s);
+            SOLVE_LAUNCHED();
+        }
+        if (two) ys = (const XT *)h->ssurf.lv[0].x;
+    } else if (two) {
         const SChain &S = h->ssurf;
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_fork, s));
         VEMG_CHECK_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
@@ -563,12 +577,15 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_join, h->side));
         ys = (const XT *)S.lv[0].x;
     }
-    // additive smoother: one V-cycle on A_bar with the trailing part of r
-    vcycle_level<XT, double>(B, 0, r + mt, (XT *)B.lv[0].x, s);
-    if (two) VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+    if (!persist) {
+        // additive smoother: one V-cycle on A_bar with the trailing part of r
+        vcycle_level<XT, double>(B, 0, r + mt, (XT *)B.lv[0].x, s);
+        if (two) VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+    }
     k_combine<XT><<<kRedBlocks, kRedThreads, 0, s>>>(h->nu, mt, sargs(h->Enon), ys, (const XT *)B.lv[0].x, z, r,
                                                      h->q, neu, flex, first, 1.0 / (double)h->nu, h->scal,
-                                                     h->red + 5 * kRedBlocks * C_Z, h->ctr + C_Z);
+                                                     h->red + 5 * kRedBlocks * C_Z, h->ctr + C_Z,
+                                                     persist ? persist_err(h) : nullptr);
     SOLVE_LAUNCHED();
 }
 
@@ -773,6 +790,7 @@ void prepare_solve(vemg_hierarchy *h, cudaStream_t s) {
     VEMG_CHECK_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     VEMG_CHECK_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (h->opts.cycle == VEMG_CYCLE_PERSISTENT) build_persist(h, s);
 }
 
 int solve(vemg_hierarchy *h, const double *b_in, double *x_out, double rtol, int max_it, vemg_info *info,
@@ -822,10 +840,15 @@ int solve(vemg_hierarchy *h, const double *b_in, double *x_out, double rtol, int
     info->b_mean = hs[S_BMEAN];
     int status;
     if (hs[S_ZERO] != 0.0) status = VEMG_OK;
+    else if (hs[S_FLAG] == 2.0) status = VEMG_ETIMEOUT;
     else if (hs[S_FLAG] != 0.0) status = VEMG_EBREAKDOWN;
     else if (hs[S_RN] <= hs[S_TOL] * hs[S_BN]) status = VEMG_OK;
     else status = VEMG_ENOTCONV;
     info->status = status;
+    if (status == VEMG_ETIMEOUT) {
+        persist_reset(h, s);
+        VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
     return status;
 }
 

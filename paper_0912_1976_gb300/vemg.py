@@ -19,6 +19,7 @@ VEMG_OK, VEMG_EINVAL, VEMG_EMESH, VEMG_ENOMEM, VEMG_ENOTCONV, VEMG_EBREAKDOWN, V
 VEMG_NEUMANN, VEMG_DIRICHLET_TOP = 0, 1
 VEMG_PREC_FP64, VEMG_PREC_FP32 = 0, 1
 VEMG_PRECOND_ADDITIVE, VEMG_PRECOND_VL_SOR, VEMG_PRECOND_SA = 0, 1, 2
+VEMG_CYCLE_PERSISTENT, VEMG_CYCLE_LAUNCHES = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ENOTCONV", 5: "EBREAKDOWN",
                 6: "ETIMEOUT", 7: "ECUDA", 8: "EINTERNAL"}
 
@@ -36,7 +37,7 @@ class vemg_csr(C.Structure):
 
 class vemg_options(C.Structure):
     _fields_ = [("bc", C.c_int), ("precision", C.c_int), ("strength", C.c_double), ("omega_p", C.c_double),
-                ("coarse_max", C.c_int), ("max_levels", C.c_int), ("precond", C.c_int)]
+                ("coarse_max", C.c_int), ("max_levels", C.c_int), ("precond", C.c_int), ("cycle", C.c_int)]
 
 
 class vemg_info(C.Structure):
@@ -50,7 +51,10 @@ class vemg_info(C.Structure):
 
 class VemgError(RuntimeError):
     def __init__(self, code, what):
-        super().__init__(f"{what}: {STATUS_NAMES.get(code, code)}")
+        msg = f"{what}: {STATUS_NAMES.get(code, code)}"
+        if code == VEMG_ECUDA and _lib is not None:
+            msg += f" ({(_lib.vemg_last_error() or b'').decode(errors='replace')})"
+        super().__init__(msg)
         self.code = code
 
 
@@ -60,6 +64,8 @@ _lib = None
 _VP, _DP, _I64 = C.c_void_p, C.c_void_p, C.c_int64
 PROTOTYPES = {
     "vemg_default_options": (None, [C.POINTER(vemg_options)]),
+    "vemg_last_error": (C.c_char_p, []),
+    "vemg_selftest_barrier": (C.c_int, [C.c_int, C.c_int, _VP]),
     "vemg_assemble": (C.c_int, [C.POINTER(vemg_mesh), C.POINTER(vemg_csr), _VP]),
     "vemg_load": (C.c_int, [C.POINTER(vemg_mesh), _DP, _DP, _VP]),
     "vemg_csr_free": (None, [C.POINTER(vemg_csr)]),
@@ -92,8 +98,9 @@ PROTOTYPES = {
     "vemg_probe": (C.c_int, [_VP, C.c_int]),
     "vemg_kernel_launches": (C.c_int, [_VP, C.POINTER(C.c_int64)]),
     "vemg_probe_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "vemg_probe_phases": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), _VP, _VP, _VP, _VP]),
 }
-VEMG_PROBE_NONE, VEMG_PROBE_SPMV_A, VEMG_PROBE_SOR, VEMG_PROBE_RESIDUAL, VEMG_PROBE_SOR_FINE = range(5)
+VEMG_PROBE_NONE, VEMG_PROBE_SPMV_A, VEMG_PROBE_SOR, VEMG_PROBE_RESIDUAL, VEMG_PROBE_SOR_FINE, VEMG_PROBE_VCYCLE = range(6)
 
 
 def lib_path() -> str:
@@ -295,6 +302,11 @@ def vemg_hierarchy_bytes(h: Hierarchy) -> int:
     return int(v.value)
 
 
+def vemg_selftest_barrier(claimed_blocks: int, launched_blocks: int, stream=None) -> int:
+    """Status of one bounded grid-barrier wait: VEMG_OK or VEMG_ETIMEOUT (returned, not raised)."""
+    return lib().vemg_selftest_barrier(claimed_blocks, launched_blocks, _stream(stream))
+
+
 def vemg_strerror(code: int) -> str:
     return lib().vemg_strerror(code).decode()
 
@@ -388,6 +400,25 @@ def vemg_probe_read(h: Hierarchy):
     ms, n, b = C.c_double(), C.c_int64(), C.c_double()
     _check(lib().vemg_probe_read(h.h, C.byref(ms), C.byref(n), C.byref(b)), "vemg_probe_read")
     return dict(ms=ms.value, launches=n.value, bytes=b.value)
+
+
+PHASE_OPS = {0: "sor", 1: "residual", 2: "transfer", 3: "prolong_add", 4: "surface_restrict", 5: "dense"}
+
+
+def vemg_probe_phases(h: Hierarchy):
+    """Per-phase cycles of the persistent preconditioner since vemg_probe(h, VEMG_PROBE_VCYCLE):
+    a list of dicts (op, level, group, cycles)."""
+    cnt = C.c_int(0)
+    lib().vemg_probe_phases(h.h, 0, C.byref(cnt), None, None, None, None)
+    n = cnt.value
+    if n == 0:
+        return []
+    op, lev, grp = (np.zeros(n, np.int32) for _ in range(3))
+    cyc = np.zeros(n, np.float64)
+    _check(lib().vemg_probe_phases(h.h, n, C.byref(cnt), C.c_void_p(op.ctypes.data), C.c_void_p(lev.ctypes.data),
+                                   C.c_void_p(grp.ctypes.data), C.c_void_p(cyc.ctypes.data)), "vemg_probe_phases")
+    return [dict(op=PHASE_OPS.get(int(op[k]), int(op[k])), level=int(lev[k]), group=int(grp[k]), cycles=float(cyc[k]))
+            for k in range(n)]
 
 
 def vemg_kernel_launches(h: Hierarchy) -> int:

@@ -239,3 +239,45 @@ def test_graph_and_stream_paths_agree():
     assert ig["iters"] == is_["iters"]
     assert r["launches"] == is_["iters"]             # one outer SpMV per iteration
     assert torch.equal(xg, xs)                         # same kernels, same order: bitwise
+
+
+# --------------------------------------------------------------------------------------------
+# the two launch structures of one preconditioner application: one persistent cooperative
+# kernel (default) and one kernel per phase; the same arithmetic row by row
+
+@pytest.mark.parametrize("precision", [V.VEMG_PREC_FP64, V.VEMG_PREC_FP32])
+@pytest.mark.parametrize("name,bc", [("zjit24", V.VEMG_NEUMANN), ("zjit64", V.VEMG_NEUMANN),
+                                     ("xyjit20", V.VEMG_NEUMANN), ("zjit24", V.VEMG_DIRICHLET_TOP)])
+def test_persistent_and_per_phase_cycles_agree(name, bc, precision):
+    m = CASES[name]()
+    vm = V.Mesh.from_inputs(m)
+    A = V.vemg_assemble(vm)
+    hp = V.vemg_setup(A, vm, V.vemg_default_options(bc=bc, precision=precision, cycle=V.VEMG_CYCLE_PERSISTENT))
+    hl = V.vemg_setup(A, vm, V.vemg_default_options(bc=bc, precision=precision, cycle=V.VEMG_CYCLE_LAUNCHES))
+    # the single steps work in the internal order of the unknowns (the non-top nodes for
+    # Dirichlet-top): compare those entries
+    nu = m.n - (V.vemg_get_size(hp, "mtop") if bc == V.VEMG_DIRICHLET_TOP else 0)
+    r = torch.from_numpy(np.random.default_rng(5).standard_normal(nu)).cuda()
+    zp, zl = V.vemg_precond(hp, r), V.vemg_precond(hl, r)
+    tol = 1e-12 if precision == V.VEMG_PREC_FP64 else 1e-5
+    assert (zp - zl).norm().item() <= tol * zl.norm().item()
+    b = torch.from_numpy(I.normal_loads(m.n, 31)).cuda()
+    xp, ip = V.vemg_solve(hp, b, rtol=1e-9)
+    xl, il = V.vemg_solve(hl, b, rtol=1e-9)
+    assert ip["status"] == il["status"] == "OK"
+    assert abs(ip["iters"] - il["iters"]) <= (0 if precision == V.VEMG_PREC_FP64 else 1)
+    assert (xp - xl).norm().item() <= (1e-10 if precision == V.VEMG_PREC_FP64 else 1e-7) * xl.norm().item()
+    # the eps = 1e-4 mesh has a true-residual floor near 3e-8 (round-off, section 6)
+    assert ip["true_relres"] <= max(2e-9, 2.0 * il["true_relres"])
+
+
+def test_bounded_barrier_wait_gives_up_and_context_survives():
+    """A grid barrier that expects more CTAs than were launched can never complete: the bounded
+    wait gives up, the status says so, and the context stays usable."""
+    assert V.vemg_selftest_barrier(2, 2) == V.VEMG_OK
+    assert V.vemg_selftest_barrier(3, 2) == V.VEMG_ETIMEOUT
+    assert V.vemg_selftest_barrier(8, 1) == V.VEMG_ETIMEOUT
+    assert V.vemg_selftest_barrier(1, 2) == V.VEMG_EINVAL
+    m, om, vm, A, h = _setup("zjit24")
+    x, info = V.vemg_solve(h, torch.from_numpy(I.normal_loads(om.n, 32)).cuda(), rtol=1e-9)
+    assert info["status"] == "OK"
