@@ -35,7 +35,7 @@ METRIC = "solves/s at FP64 rel-res 1e-8"
 
 
 PRECONDS = {"additive": 0, "vl_sor": 1, "sa": 2}
-CYCLES = {"persistent": 0, "launches": 1}
+CYCLES = {"persistent": 0, "launches": 1, "auto": 2}
 
 
 def parse():
@@ -45,8 +45,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vemg", choices=["vemg", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
-    ap.add_argument("--cycle", default="persistent", choices=["persistent", "launches"],
-                    help="one cooperative kernel per preconditioner application, or one kernel per phase")
+    ap.add_argument("--cycle", default="auto", choices=["auto", "persistent", "launches"],
+                    help="one cooperative kernel per preconditioner application, one kernel per phase, or the "
+                         "library's choice by precision")
     ap.add_argument("--precond", default="additive", choices=list(PRECONDS),
                     help="additive (the paper's preconditioner), vl_sor or sa (its two comparison forms)")
     ap.add_argument("--workload", default=WORKLOAD)
@@ -74,7 +75,8 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi samples (every 50 ms) during the timed region."""
+    """nvidia-smi samples (every 200 ms) during the timed region. Each query takes driver time that
+    can delay the solve's launches, so the interval is kept long."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -84,7 +86,7 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={device_index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -225,7 +227,7 @@ def workload_config(args, n):
 # --------------------------------------------------------------------------------------------
 # the GPU path
 
-def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe):
+def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe, persistent=False):
     """Time args.steps solves (device-resident inputs), then the same through the host-buffer
     entry point, then (optionally) per-kernel-class probes."""
     nb = len(B)
@@ -305,7 +307,7 @@ def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe):
     if probe and not batched:
         # the persistent cycle (one kernel per preconditioner application) or, with per-phase
         # launches, its kernel classes
-        if args.cycle == "persistent":
+        if persistent:
             kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "vcycle": V.VEMG_PROBE_VCYCLE}
         else:
             kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "sor_fine": V.VEMG_PROBE_SOR_FINE, "sor_all": V.VEMG_PROBE_SOR,
@@ -436,7 +438,10 @@ def main():
             cycle=CYCLES[args.cycle]))
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
-        r = measure(args, h, B, n, ws, rank, local, dist, V, torch, probe=not args.no_probe)
+        # VEMG_CYCLE_AUTO resolves to the persistent kernel for FP64 V-cycles
+        persistent = args.cycle == "persistent" or (args.cycle == "auto" and prec == "fp64")
+        r = measure(args, h, B, n, ws, rank, local, dist, V, torch, probe=not args.no_probe, persistent=persistent)
+        r["cycle"] = "persistent" if persistent else "launches"
         r["setup_s"] = setup_s
         r["hierarchy_bytes"] = V.vemg_hierarchy_bytes(h)
         res[prec] = r
@@ -470,7 +475,7 @@ def main():
             comparator = {"name": "plain FP64 PCG (same hierarchy, FP64 V-cycles)", "value": f["value"],
                           "iters": f["iters"][0], "ms_per_step": f["ms_per_step"],
                           "e2e": f["e2e"]["value"], "true_relres_max": f["true_relres_max"],
-                          "speedup_of_value": head["value"] / f["value"]}
+                          "cycle": f["cycle"], "speedup_of_value": head["value"] / f["value"]}
         line = {"metric": METRIC, "value": head["value"], "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,

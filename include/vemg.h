@@ -63,6 +63,8 @@ extern "C" {
 /* how a preconditioner application is launched */
 #define VEMG_CYCLE_PERSISTENT 0  /* one cooperative kernel runs every phase of the V-cycles */
 #define VEMG_CYCLE_LAUNCHES 1    /* one kernel per phase (colour sweep, residual, transfer) */
+#define VEMG_CYCLE_AUTO 2        /* the faster of the two as measured on GB300: persistent for FP64
+                                    V-cycles, one kernel per phase for FP32 ones */
 
 /* precision of the preconditioner; the outer Krylov loop is always FP64 */
 #define VEMG_PREC_FP64 0   /* everything FP64, CG outer loop */
@@ -116,7 +118,7 @@ typedef struct vemg_info {
 typedef struct vemg_hierarchy vemg_hierarchy;
 
 /* Fill opts with the paper's parameters (section 6): strength 0.01, omega_p = 2/3, Neumann,
-   FP64, coarse_max = 512, max_levels = 10, the additive preconditioner, persistent cycles. */
+   FP64, coarse_max = 512, max_levels = 10, the additive preconditioner, VEMG_CYCLE_AUTO. */
 void vemg_default_options(vemg_options *opts);
 
 /* Assemble the P1 stiffness matrix A_ij = integral grad N_i . grad N_j in physical coordinates

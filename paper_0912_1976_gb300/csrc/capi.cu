@@ -113,7 +113,7 @@ void vemg_default_options(vemg_options *o) {
     o->coarse_max = 512;
     o->max_levels = 10;
     o->precond = VEMG_PRECOND_ADDITIVE;
-    o->cycle = VEMG_CYCLE_PERSISTENT;
+    o->cycle = VEMG_CYCLE_AUTO;
 }
 
 const char *vemg_last_error(void) { return last_cuda_error(); }
@@ -188,9 +188,11 @@ int vemg_setup(const vemg_csr *A, const vemg_mesh *mesh, const vemg_options *opt
             !(o.omega_p > 0.0) || o.coarse_max < 1 || o.coarse_max > 1024 || o.max_levels < 1 ||
             o.max_levels > kMaxLevels || o.precond < VEMG_PRECOND_ADDITIVE || o.precond > VEMG_PRECOND_SA ||
             (o.precond == VEMG_PRECOND_VL_SOR && o.bc != VEMG_NEUMANN) ||
-            (o.cycle != VEMG_CYCLE_PERSISTENT && o.cycle != VEMG_CYCLE_LAUNCHES))
+            (o.cycle != VEMG_CYCLE_PERSISTENT && o.cycle != VEMG_CYCLE_LAUNCHES && o.cycle != VEMG_CYCLE_AUTO))
             return VEMG_EINVAL;
         h = new vemg_hierarchy();
+        if (o.cycle == VEMG_CYCLE_AUTO)
+            o.cycle = o.precision == VEMG_PREC_FP64 ? VEMG_CYCLE_PERSISTENT : VEMG_CYCLE_LAUNCHES;
         h->opts = o;
         h->bc = o.bc;
         h->precision = o.precision;

@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_spmv(int s0, int s1, const 
                                                           const int *__restrict__ width, const int *__restrict__ col,
                                                           const VT *__restrict__ v, const XT *__restrict__ x,
                                                           YT *__restrict__ y, int add) {
+    pdl_begin();
     int s = s0 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (s >= s1 || lane >= nrow[s]) return;
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_sor(int s0, int s1, const i
                                                          const int *__restrict__ width, const int *__restrict__ col,
                                                          const VT *__restrict__ v, const VT *__restrict__ dinv,
                                                          const BT *__restrict__ b, XT *x, int lim) {
+    pdl_begin();
     int s = s0 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (s >= s1 || lane >= nrow[s]) return;
@@ -167,6 +169,7 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_residual(int nsl, const int
                                                               const VT *__restrict__ v, const VT *__restrict__ diag,
                                                               const BT *__restrict__ b, const XT *__restrict__ x,
                                                               XT *__restrict__ r) {
+    pdl_begin();
     int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (s >= nsl || lane >= nrow[s]) return;
@@ -178,6 +181,7 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_residual(int nsl, const int
 // x = G b for the dense coarsest inverse (one warp per row, FP64 accumulation)
 template <class XT, class BT>
 __global__ void k_dense_mv(int n, const double *__restrict__ Gm, const BT *__restrict__ b, XT *__restrict__ x) {
+    pdl_begin();
     int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
     if (row >= n) return;
     double s = 0.0;
@@ -194,7 +198,7 @@ template <class VT, class XT, class YT, class AT>
 static void sell_spmv(const Sell &S, const XT *x, YT *y, int add, cudaStream_t s) {
     if (S.nslices == 0) return;
     int64_t threads = (int64_t)S.nslices * 32;
-    k_sell_spmv<VT, XT, YT, AT><<<grid_for(threads, kSellBlock), kSellBlock, 0, s>>>(
+    pdl_launch(k_sell_spmv<VT, XT, YT, AT>, grid_for(threads, kSellBlock), kSellBlock, s, 
         0, S.nslices, S.row0, S.nrow, S.off, S.width, S.col, (const VT *)S.v, x, y, add);
     SOLVE_LAUNCHED();
 }
@@ -213,7 +217,7 @@ static void sor_sweep(const SLevel &L, const BT *b, XT *x, bool forward, bool fr
                        (double)sizeof(XT) * L.n / L.ncolours;
         ProbeScope ps(fine ? PROBE_SOR_FINE : PROBE_SOR, bytes, s);
         int64_t threads = (int64_t)(s1 - s0) * 32;
-        k_sell_sor<XT, XT, BT><<<grid_for(threads, kSellBlock), kSellBlock, 0, s>>>(
+        pdl_launch(k_sell_sor<XT, XT, BT>, grid_for(threads, kSellBlock), kSellBlock, s, 
             s0, s1, L.A.row0, L.A.nrow, L.A.off, L.A.width, L.A.col, (const XT *)L.A.v, (const XT *)L.dinv, b, x, lim);
         SOLVE_LAUNCHED();
     }
@@ -223,7 +227,7 @@ template <class XT, class BT>
 static void residual(const SLevel &L, const BT *b, const XT *x, XT *r, cudaStream_t s) {
     ProbeScope ps(PROBE_RESIDUAL, sell_bytes(L.A.nnz, sizeof(XT), L.n, 5.0 * sizeof(XT)), s);
     int64_t threads = (int64_t)L.A.nslices * 32;
-    k_sell_residual<XT, XT, BT><<<grid_for(threads, kSellBlock), kSellBlock, 0, s>>>(
+    pdl_launch(k_sell_residual<XT, XT, BT>, grid_for(threads, kSellBlock), kSellBlock, s, 
         L.A.nslices, L.A.row0, L.A.nrow, L.A.off, L.A.width, L.A.col, (const XT *)L.A.v, (const XT *)L.diag, b, x, r);
     SOLVE_LAUNCHED();
 }
@@ -235,7 +239,7 @@ static void vcycle_level(const SChain &C, int l, const BT *b, XT *x, cudaStream_
     const bool fine = C.is_bar && l == 0;
     if (l == C.nlev - 1) {
         if (C.direct) {
-            k_dense_mv<XT, BT><<<grid_for(C.nc, 8), 256, 0, s>>>(C.nc, C.G, b, x);
+            pdl_launch(k_dense_mv<XT, BT>, grid_for(C.nc, 8), 256, s, C.nc, C.G, b, x);
             SOLVE_LAUNCHED();
             return;
         }
@@ -321,6 +325,7 @@ static SellArgs sargs(const Sell &S) {
 __global__ void __launch_bounds__(kRedThreads) k_spmv_pq(SellArgs A, const double *__restrict__ p,
                                                          double *__restrict__ q, double *sc, double *part,
                                                          unsigned *ctr) {
+    pdl_begin();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double acc[1] = {0.0};
     for (int s = blockIdx.x * (kRedThreads / 32) + warp; s < A.nsl; s += kRedBlocks * (kRedThreads / 32)) {
@@ -349,6 +354,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(int n, const double *
                                                            double *__restrict__ r, double *sc, double *part,
                                                            unsigned *ctr, cudaGraphConditionalHandle handle,
                                                            int use_cond) {
+    pdl_begin();
     double a = sc[S_ALPHA];
     double acc[1] = {0.0};
     constexpr int stride = kRedBlocks * kRedThreads;
@@ -397,6 +403,7 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(int nu, int mtop, SellA
                                                          int neumann, int flexible, int first, double inv_n,
                                                          double *sc, double *part, unsigned *ctr,
                                                          const int *__restrict__ perr) {
+    pdl_begin();
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     constexpr int stride = kRedBlocks * kRedThreads;
     const bool dots_q = flexible && !first;
@@ -465,6 +472,7 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(int nu, int mtop, SellA
 
 // p = (z - mu) + beta p
 __global__ void k_update_p(int n, const double *__restrict__ sc, const double *__restrict__ z, double *__restrict__ p) {
+    pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double mu = sc[S_MU], beta = sc[S_BETA];
     if (i < n) p[i] = (z[i] - mu) + beta * p[i];
@@ -473,6 +481,7 @@ __global__ void k_update_p(int n, const double *__restrict__ sc, const double *_
 // sum of a vector; the last block stores the mean in sc[slot]
 __global__ void __launch_bounds__(kRedThreads) k_mean(int n, const double *__restrict__ a, double inv_n, int slot,
                                                       double *sc, double *part, unsigned *ctr) {
+    pdl_begin();
     double acc[1] = {0.0};
     constexpr int stride = kRedBlocks * kRedThreads;
     for (int i0 = blockIdx.x * kRedThreads + threadIdx.x; i0 < n; i0 += kRows * stride) {
@@ -492,6 +501,7 @@ __global__ void __launch_bounds__(kRedThreads) k_prepare(int n, int neumann, dou
                                                          double *__restrict__ r, double *__restrict__ x,
                                                          double *__restrict__ p, double *sc, double *part,
                                                          unsigned *ctr) {
+    pdl_begin();
     double mu = neumann ? sc[S_BMEAN] : 0.0;
     double acc[1] = {0.0};
     constexpr int stride = kRedBlocks * kRedThreads;
@@ -523,6 +533,7 @@ __global__ void __launch_bounds__(kRedThreads) k_prepare(int n, int neumann, dou
 }
 
 __global__ void k_sub_scalar(int n, double *__restrict__ a, const double *__restrict__ sc, int slot) {
+    pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] -= sc[slot];
 }
@@ -531,6 +542,7 @@ __global__ void k_sub_scalar(int n, double *__restrict__ a, const double *__rest
 __global__ void __launch_bounds__(kRedThreads) k_true_res(SellArgs A, const double *__restrict__ x,
                                                           const double *__restrict__ b, double *sc, double *part,
                                                           unsigned *ctr) {
+    pdl_begin();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double acc[1] = {0.0};
     for (int s = blockIdx.x * (kRedThreads / 32) + warp; s < A.nsl; s += kRedBlocks * (kRedThreads / 32)) {
@@ -582,7 +594,7 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
         vcycle_level<XT, double>(B, 0, r + mt, (XT *)B.lv[0].x, s);
         if (two) VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
     }
-    k_combine<XT><<<kRedBlocks, kRedThreads, 0, s>>>(h->nu, mt, sargs(h->Enon), ys, (const XT *)B.lv[0].x, z, r,
+    pdl_launch(k_combine<XT>, kRedBlocks, kRedThreads, s, h->nu, mt, sargs(h->Enon), ys, (const XT *)B.lv[0].x, z, r,
                                                      h->q, neu, flex, first, 1.0 / (double)h->nu, h->scal,
                                                      h->red + 5 * kRedBlocks * C_Z, h->ctr + C_Z,
                                                      persist ? persist_err(h) : nullptr);
@@ -597,7 +609,7 @@ static void precond_solve_order(vemg_hierarchy *h, const double *r, double *z, i
 // q = A p of the outer loop, with (p, q) and alpha
 static void spmv_outer(vemg_hierarchy *h, const double *x, double *y, cudaStream_t s) {
     ProbeScope ps(PROBE_SPMV_A, sell_bytes(h->Aop.nnz, 8.0, h->Aop.n, 24.0), s);   // p read twice, q write
-    k_spmv_pq<<<kRedBlocks, kRedThreads, 0, s>>>(sargs(h->Aop), x, y, h->scal, h->red + 5 * kRedBlocks * C_SPMV,
+    pdl_launch(k_spmv_pq, kRedBlocks, kRedThreads, s, sargs(h->Aop), x, y, h->scal, h->red + 5 * kRedBlocks * C_SPMV,
                                                  h->ctr + C_SPMV);
     SOLVE_LAUNCHED();
 }
@@ -642,22 +654,22 @@ static void phase_pre(vemg_hierarchy *h, cudaStream_t s) {
     const bool neu = h->bc == VEMG_NEUMANN;
     const int nu = h->nu;
     if (neu) {
-        k_mean<<<kRedBlocks, kRedThreads, 0, s>>>(nu, h->b, 1.0 / (double)nu, S_BMEAN, h->scal, part_of(h, C_SUMB),
+        pdl_launch(k_mean, kRedBlocks, kRedThreads, s, nu, h->b, 1.0 / (double)nu, S_BMEAN, h->scal, part_of(h, C_SUMB),
                                                   h->ctr + C_SUMB);
         SOLVE_LAUNCHED();
     }
-    k_prepare<<<kRedBlocks, kRedThreads, 0, s>>>(nu, neu, h->b, h->r, h->x, h->p, h->scal, part_of(h, C_PREP),
+    pdl_launch(k_prepare, kRedBlocks, kRedThreads, s, nu, neu, h->b, h->r, h->x, h->p, h->scal, part_of(h, C_PREP),
                                                  h->ctr + C_PREP);
     SOLVE_LAUNCHED();
     precond_solve_order(h, h->r, h->z, 1, s);
-    k_update_p<<<grid_for(nu, 256), 256, 0, s>>>(nu, h->scal, h->z, h->p);
+    pdl_launch(k_update_p, grid_for(nu, 256), 256, s, nu, h->scal, h->z, h->p);
     SOLVE_LAUNCHED();
 }
 
 // q = A p, alpha, x and r updates, ||r||, continuation
 static void phase_step(vemg_hierarchy *h, cudaStream_t s, cudaGraphConditionalHandle hd, int use_cond) {
     spmv_outer(h, h->p, h->q, s);
-    k_update_xr<<<kRedBlocks, kRedThreads, 0, s>>>(h->nu, h->p, h->q, h->x, h->r, h->scal, part_of(h, C_XR),
+    pdl_launch(k_update_xr, kRedBlocks, kRedThreads, s, h->nu, h->p, h->q, h->x, h->r, h->scal, part_of(h, C_XR),
                                                    h->ctr + C_XR, hd, use_cond);
     SOLVE_LAUNCHED();
 }
@@ -665,7 +677,7 @@ static void phase_step(vemg_hierarchy *h, cudaStream_t s, cudaGraphConditionalHa
 // new preconditioned residual and search direction
 static void phase_direction(vemg_hierarchy *h, cudaStream_t s) {
     precond_solve_order(h, h->r, h->z, 0, s);
-    k_update_p<<<grid_for(h->nu, 256), 256, 0, s>>>(h->nu, h->scal, h->z, h->p);
+    pdl_launch(k_update_p, grid_for(h->nu, 256), 256, s, h->nu, h->scal, h->z, h->p);
     SOLVE_LAUNCHED();
 }
 
@@ -673,13 +685,13 @@ static void phase_post(vemg_hierarchy *h, cudaStream_t s) {
     const bool neu = h->bc == VEMG_NEUMANN;
     const int nu = h->nu;
     if (neu) {
-        k_mean<<<kRedBlocks, kRedThreads, 0, s>>>(nu, h->x, 1.0 / (double)nu, S_XMEAN, h->scal, part_of(h, C_SUMX),
+        pdl_launch(k_mean, kRedBlocks, kRedThreads, s, nu, h->x, 1.0 / (double)nu, S_XMEAN, h->scal, part_of(h, C_SUMX),
                                                   h->ctr + C_SUMX);
         SOLVE_LAUNCHED();
-        k_sub_scalar<<<grid_for(nu, 256), 256, 0, s>>>(nu, h->x, h->scal, S_XMEAN);
+        pdl_launch(k_sub_scalar, grid_for(nu, 256), 256, s, nu, h->x, h->scal, S_XMEAN);
         SOLVE_LAUNCHED();
     }
-    k_true_res<<<kRedBlocks, kRedThreads, 0, s>>>(sargs(h->Aop), h->x, h->b, h->scal, part_of(h, C_TRUE),
+    pdl_launch(k_true_res, kRedBlocks, kRedThreads, s, sargs(h->Aop), h->x, h->b, h->scal, part_of(h, C_TRUE),
                                                   h->ctr + C_TRUE);
     SOLVE_LAUNCHED();
 }

@@ -19,7 +19,7 @@ VEMG_OK, VEMG_EINVAL, VEMG_EMESH, VEMG_ENOMEM, VEMG_ENOTCONV, VEMG_EBREAKDOWN, V
 VEMG_NEUMANN, VEMG_DIRICHLET_TOP = 0, 1
 VEMG_PREC_FP64, VEMG_PREC_FP32 = 0, 1
 VEMG_PRECOND_ADDITIVE, VEMG_PRECOND_VL_SOR, VEMG_PRECOND_SA = 0, 1, 2
-VEMG_CYCLE_PERSISTENT, VEMG_CYCLE_LAUNCHES = 0, 1
+VEMG_CYCLE_PERSISTENT, VEMG_CYCLE_LAUNCHES, VEMG_CYCLE_AUTO = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ENOTCONV", 5: "EBREAKDOWN",
                 6: "ETIMEOUT", 7: "ECUDA", 8: "EINTERNAL"}
 
