@@ -318,6 +318,38 @@ __global__ void __launch_bounds__(kBT) k_bsums(int64_t N, int K, BSums d, double
     bblock_partials<NS>(acc, K, part);
 }
 
+// the preconditioner's sums over z, r (and q): s0 = sum z, s1 = sum r z, s2 = sum r
+// [, s3 = sum z q, s4 = sum q]; each vector is loaded once per element (the generic kernel
+// above would load z three times and hold 80 values per thread). Same order of accumulation.
+template <int NS>
+__global__ void __launch_bounds__(kBT, 2) k_bsums_zrq(int64_t N, int K, const double *__restrict__ z,
+                                                      const double *__restrict__ r, const double *__restrict__ q,
+                                                      double *part) {
+    double acc[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) acc[s] = 0.0;
+    int64_t base = (int64_t)blockIdx.x * kBT * kBE + threadIdx.x;
+    double vz[kBE], vr[kBE], vq[kBE];
+#pragma unroll
+    for (int j = 0; j < kBE; ++j) {
+        int64_t e = base + (int64_t)j * kBT;
+        vz[j] = e < N ? z[e] : 0.0;
+        vr[j] = e < N ? r[e] : 0.0;
+        vq[j] = (NS == 5 && e < N) ? q[e] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kBE; ++j) {
+        acc[0] += vz[j] * 1.0;
+        acc[1] += vr[j] * vz[j];
+        acc[2] += vr[j] * 1.0;
+        if (NS == 5) {
+            acc[3] += vz[j] * vq[j];
+            acc[4] += vq[j] * 1.0;
+        }
+    }
+    bblock_partials<NS>(acc, K, part);
+}
+
 enum { ST_MEAN_B = 0, ST_BN, ST_ALPHA, ST_RN, ST_BETA, ST_MEAN_X, ST_TRUE };
 
 // stage 2: one block per column
@@ -570,9 +602,13 @@ static void bprecond_any(vemg_hierarchy *h, BatchWork *W, int first, cudaStream_
     int64_t N = (int64_t)h->nu * W->K;
     bool flex = h->precision != VEMG_PREC_FP64;
     (void)first;
-    BSums d{{W->Z, W->R, W->R, W->Z, W->Q}, {nullptr, W->Z, nullptr, W->Q, nullptr}, flex ? 5 : 3};
-    bsums(W, N, d, s);
-    bstage2(h, W, ST_BETA, d.ns, N, first, s);
+    const int ns = flex ? 5 : 3;
+    if (flex)
+        k_bsums_zrq<5><<<stage1_blocks(N), kBT, 0, s>>>(N, W->K, W->Z, W->R, W->Q, W->part);
+    else
+        k_bsums_zrq<3><<<stage1_blocks(N), kBT, 0, s>>>(N, W->K, W->Z, W->R, nullptr, W->part);
+    BATCH_LAUNCHED();
+    bstage2(h, W, ST_BETA, ns, N, first, s);
 }
 
 // b -= mean (Neumann), r = b, x = p = 0, ||b|| per column; the iterations themselves start in the
@@ -836,11 +872,26 @@ int solve_batch(vemg_hierarchy *h, int k, const double *Bin, int64_t ldb, double
     BATCH_LAUNCHED();
     k_bgather<<<grid_for((int64_t)nu * K, 256), 256, 0, s>>>(nu, K, k, ldb, W->caller_of, Bin, W->B);
     BATCH_LAUNCHED();
+    // with a probe on, the same phases are launched on the stream (profilers see every kernel)
+    const bool use_graph = h->probe.kind == PROBE_NONE;
     if (!W->graphs) build_batch_graphs(h, W);
     BatchGraphs *G = W->graphs;
-    VEMG_CHECK_CUDA(cudaGraphLaunch(G->pre, s));
-    VEMG_CHECK_CUDA(cudaGraphLaunch(G->loop, s));
-    VEMG_CHECK_CUDA(cudaGraphLaunch(G->post, s));
+    if (use_graph) {
+        VEMG_CHECK_CUDA(cudaGraphLaunch(G->pre, s));
+        VEMG_CHECK_CUDA(cudaGraphLaunch(G->loop, s));
+        VEMG_CHECK_CUDA(cudaGraphLaunch(G->post, s));
+    } else {
+        bphase_pre(h, W, s);
+        for (;;) {
+            double cont = 0.0;
+            VEMG_CHECK_CUDA(cudaMemcpyAsync(&cont, gsc(W) + G_CONT, sizeof(double), cudaMemcpyDeviceToHost, s));
+            VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+            if (cont == 0.0) break;
+            bphase_direction(h, W, s);
+            bphase_step(h, W, s, 0, 0);
+        }
+        bphase_post(h, W, s);
+    }
     std::vector<double> hs(B_COUNT * K + G_COUNT);
     VEMG_CHECK_CUDA(cudaMemcpyAsync(hs.data(), W->sc, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s));
     int ntop = h->bc == VEMG_DIRICHLET_TOP ? h->mtop : 0;
@@ -849,7 +900,7 @@ int solve_batch(vemg_hierarchy *h, int k, const double *Bin, int64_t ldb, double
     BATCH_LAUNCHED();
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
     int rounds = (int)hs[B_COUNT * K + G_ITERS];
-    h->launches += G->k_pre + G->k_post + (int64_t)rounds * G->k_body;
+    if (use_graph) h->launches += G->k_pre + G->k_post + (int64_t)rounds * G->k_body;
     int rc = VEMG_OK;
     for (int c = 0; c < k; ++c) {
         vemg_info &in = infos[c];
