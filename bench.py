@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (0: 0.8 x saturation)")
     ap.add_argument("--case", default="",
                     help="profiling case NXxNYxNZ (z-jitter 0.3, eps 1e-3): two untimed solves, then exit")
+    ap.add_argument("--spectrum", action="store_true",
+                    help="the section 4 study: condition estimates of A and M^-1 A over eps (not a timing run)")
     ap.add_argument("--stream-path", action="store_true",
                     help="with --case: launch the solve's kernels on the stream, not from CUDA graphs")
     ap.add_argument("--rhs", type=int, default=0,
@@ -398,12 +400,51 @@ def run_case(args):
     return 0
 
 
+def run_spectrum(args):
+    """Section 4 study: Lanczos estimates (from the CG coefficients of each solve) of the extreme
+    eigenvalues and the condition number of A and of M^-1 A for the three preconditioners, over
+    eps, on a layered (z-jittered) and a vertically unstructured (xy-jittered) mesh."""
+    import torch
+    from paper_0912_1976_gb300 import inputs as I
+    from paper_0912_1976_gb300 import vemg as V
+    nx, nz = 64, 16
+    kinds = {"layered": dict(z_jitter=0.3, xy_jitter=0.0), "unstructured": dict(z_jitter=0.3, xy_jitter=0.2)}
+    pcs = {"none": V.VEMG_PRECOND_NONE, "additive": V.VEMG_PRECOND_ADDITIVE, "vl_sor": V.VEMG_PRECOND_VL_SOR,
+           "sa": V.VEMG_PRECOND_SA}
+    rows = []
+    for kind, jit in kinds.items():
+        for eps in (1e-1, 1e-2, 1e-3, 1e-4):
+            m = I.make_mesh(nx, nx, nz, I.depth_sines(eps), seed=7, **jit)
+            vm = V.Mesh.from_inputs(m)
+            A = V.vemg_assemble(vm)
+            b = torch.from_numpy(I.normal_loads(m.n, 11)).cuda()
+            for name, pc in pcs.items():
+                h = V.vemg_setup(A, vm, V.vemg_default_options(precond=pc, precision=V.VEMG_PREC_FP64))
+                t0 = time.perf_counter()
+                _, info = V.vemg_solve(h, b, rtol=1e-8, max_it=4096)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                a, bt = V.vemg_solve_coefficients(h)
+                lo, hi = V.vemg_lanczos_extremes(a, bt)
+                rows.append({"mesh": kind, "eps": eps, "preconditioner": name, "iters": info["iters"],
+                             "status": info["status"], "lambda_min": lo, "lambda_max": hi, "cond": hi / lo,
+                             "cond_is_lower_bound": info["status"] != "OK", "solve_s": dt})
+                h.destroy()
+            A.free()
+    print(json.dumps({"study": "spectrum (section 4): Lanczos condition estimates from CG coefficients",
+                      "mesh": f"{nx}x{nx}x{nz} extruded hex->6 tets, H = eps (1 + 0.5 sin sin), seed 7",
+                      "rtol": 1e-8, "max_it": 4096, "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.case:
         return run_case(args)
+    if args.spectrum:
+        return run_spectrum(args)
     if args.serve:
         return run_serve(args)
     import torch

@@ -59,6 +59,7 @@ extern "C" {
 #define VEMG_PRECOND_ADDITIVE 0  /* vertical lumping + additive smoother, Eq. ourpreconditioner (section 5.5) */
 #define VEMG_PRECOND_VL_SOR 1    /* vertical lumping as the first coarsening of a V-cycle on A with SOR smoothing */
 #define VEMG_PRECOND_SA 2        /* smoothed-aggregation AMG on A */
+#define VEMG_PRECOND_NONE 3      /* none: plain CG, for the spectrum of A itself (section 4); FP64 only */
 
 /* how a preconditioner application is launched */
 #define VEMG_CYCLE_PERSISTENT 0  /* one cooperative kernel runs every phase of the V-cycles */
@@ -219,6 +220,23 @@ int vemg_set_allocator(void *(*alloc)(size_t bytes, void *ctx), void (*free_fn)(
 
 /* Human-readable name of a status code (static string). */
 const char *vemg_strerror(int status);
+
+/* ---- spectrum (section 4): the CG coefficients of a solve give the Lanczos tridiagonal of the
+   preconditioned operator, whose extreme eigenvalues converge to those of M^-1 A (of A with
+   VEMG_PRECOND_NONE; on the complement of the constants with Neumann) ---- */
+
+/* Coefficients of the last vemg_solve on h: alpha[k] = (r_k, z_k) / (p_k, A p_k) and beta[k] =
+   (r_k, z_k) / (r_{k-1}, z_{k-1}) (beta[0] = 0), k < *count = iterations of that solve (at most
+   4096 are kept). Host arrays of capacity entries; VEMG_EINVAL if capacity < *count (with *count
+   set) or if the V-cycles are FP32 (flexible CG has no Lanczos recurrence). Synchronous. */
+int vemg_solve_coefficients(vemg_hierarchy *h, int capacity, double *alpha, double *beta, int *count);
+
+/* Smallest and largest eigenvalue of the tridiagonal T with T_00 = 1/alpha_0,
+   T_kk = 1/alpha_k + beta_k/alpha_{k-1}, T_{k,k+1} = sqrt(beta_{k+1})/alpha_k, for k < count
+   (Sturm-sequence bisection, relative accuracy ~1e-14). Host arrays; VEMG_EINVAL if count < 1
+   or a coefficient is not positive. Touches no GPU. */
+int vemg_lanczos_extremes(const double *alpha, const double *beta, int count, double *lambda_min,
+                          double *lambda_max);
 
 /* The CUDA error behind the last VEMG_ECUDA returned on this host thread: the runtime's message,
    the failing call and its source location. Empty if none. The string is owned by the library

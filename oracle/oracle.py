@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 BC_NEUMANN = 0
 BC_DIRICHLET_TOP = 1
 # the three preconditioners of section 6
-PC_ADDITIVE, PC_VL_SOR, PC_SA = 0, 1, 2
+PC_ADDITIVE, PC_VL_SOR, PC_SA, PC_NONE = 0, 1, 2, 3
 STATUS = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ENOTCONV", 5: "EBREAKDOWN"}
 
 # the paper's smoothed-aggregation parameters (section 6)
@@ -55,7 +55,8 @@ def lib():
         L.or_size.argtypes = [C.c_void_p, C.c_char_p, C.c_int, C.c_int]
         L.or_get_csr.argtypes = [C.c_void_p, C.c_char_p, C.c_int, C.c_int, ip, ip, dp]
         L.or_get_int.argtypes = [C.c_void_p, C.c_char_p, C.c_int, C.c_int, ip]
-        L.or_solve.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_int, C.c_int, ip, dp, dp, dp, C.c_int]
+        L.or_solve.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_int, C.c_int, ip, dp, dp, dp, C.c_int, dp,
+                               C.c_int]
         L.or_precond.argtypes = [C.c_void_p, dp, dp]
         L.or_spmv.argtypes = [C.c_void_p, dp, dp]
         L.or_load.argtypes = [C.c_void_p, dp, dp]
@@ -158,10 +159,16 @@ class Problem:
         it = C.c_int(0)
         rr, tr = C.c_double(0), C.c_double(0)
         hist = np.zeros(hist_len)
+        coef = np.zeros(2 * maxit + 2)
         st = lib().or_solve(self.h, _p(b, C.c_double), _p(x, C.c_double), tol, maxit, int(flexible),
-                            C.byref(it), C.byref(rr), C.byref(tr), _p(hist, C.c_double), hist_len)
-        return dict(x=x, iters=it.value, relres=rr.value, true_relres=tr.value, status=STATUS[st],
-                    hist=hist[:min(it.value, hist_len)])
+                            C.byref(it), C.byref(rr), C.byref(tr), _p(hist, C.c_double), hist_len,
+                            _p(coef, C.c_double), len(coef))
+        k = it.value
+        # alpha_0..alpha_{k-1}; beta_0 = 0 and beta_1..beta_{k-1} (the last beta is never used)
+        alpha = coef[0:2 * k:2].copy()
+        beta = np.concatenate([[0.0], coef[1:2 * k - 1:2]]) if k > 0 else np.zeros(0)
+        return dict(x=x, iters=k, relres=rr.value, true_relres=tr.value, status=STATUS[st],
+                    hist=hist[:min(k, hist_len)], alpha=alpha, beta=beta)
 
     def nunk(self):
         return self.n if self.bc == BC_NEUMANN else self.n - self.mtop

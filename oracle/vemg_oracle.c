@@ -56,6 +56,7 @@
 #define PC_ADDITIVE 0   /* vertical lumping + additive smoother, Eq. ourpreconditioner (section 5.5) */
 #define PC_VL_SOR 1     /* vertical lumping as the first coarsening of a V-cycle with SOR smoothing on A */
 #define PC_SA 2         /* smoothed-aggregation AMG on A */
+#define PC_NONE 3       /* no preconditioner: plain CG (the spectrum of A itself, section 4) */
 
 #define MAX_LEVELS_CAP 16
 
@@ -989,12 +990,12 @@ void *or_setup(int n, const double *xyz, int ntet, const int *tets, const unsign
                int natural_order, int precond, int *status) {
     *status = OR_OK;
     if (n <= 0 || ntet <= 0 || (bc != BC_NEUMANN && bc != BC_DIRICHLET_TOP) || precond < PC_ADDITIVE ||
-        precond > PC_SA || (precond == PC_VL_SOR && bc != BC_NEUMANN)) { *status = OR_EINVAL; return NULL; }
+        precond > PC_NONE || (precond == PC_VL_SOR && bc != BC_NEUMANN)) { *status = OR_EINVAL; return NULL; }
     for (int e = 0; e < 4 * ntet; ++e) if (tets[e] < 0 || tets[e] >= n) { *status = OR_EMESH; return NULL; }
     problem *h = (problem *)xcalloc(1, sizeof(problem));
     h->n = n; h->bc = bc; h->ntet = ntet;
     /* with Dirichlet on top, smoothed aggregation on A_bar is the additive preconditioner itself */
-    h->precond = bc == BC_DIRICHLET_TOP ? PC_ADDITIVE : precond;
+    h->precond = (bc == BC_DIRICHLET_TOP && precond != PC_NONE) ? PC_ADDITIVE : precond;
     h->tets = (int *)xcalloc((size_t)ntet * 4, sizeof(int));
     memcpy(h->tets, tets, sizeof(int) * (size_t)ntet * 4);
     h->xyz = (double *)xcalloc((size_t)n * 3, sizeof(double));
@@ -1064,6 +1065,7 @@ void or_free(void *hp) {
 void or_precond(void *hp, const double *r, double *z) {
     problem *h = (problem *)hp;
     int mt = h->mtop, n = h->n;
+    if (h->precond == PC_NONE) { memcpy(z, r, sizeof(double) * (size_t)(h->n - (h->bc == BC_NEUMANN ? 0 : mt))); return; }
     if (h->bc == BC_DIRICHLET_TOP) { vcycle(&h->bar, 0, r, z); return; }
     if (h->precond != PC_ADDITIVE) { vcycle(&h->one, 0, r, z); return; }
     level *s0 = &h->surf.lv[0];
@@ -1086,8 +1088,12 @@ void or_spmv(void *hp, const double *x, double *y) {
    Neumann: b is projected to mean zero, each preconditioned residual z is projected to mean
    zero before use, and x is returned with zero mean. Stops when ||r_k||_2 <= tol ||b||_2 on the
    recursively updated residual. b and x are in the caller's node ordering. */
+/* Preconditioned CG (section 6) on the unknowns of the boundary condition. coef (optional):
+   coef[2k] = alpha_k, coef[2k + 1] = beta_{k+1}, the coefficients from which the Lanczos
+   tridiagonal of the preconditioned operator follows (plain CG only, flexible = 0). */
 int or_solve(void *hp, const double *b_orig, double *x_orig, double tol, int maxit, int flexible,
-             int *iters, double *relres, double *true_relres, double *hist, int hist_len) {
+             int *iters, double *relres, double *true_relres, double *hist, int hist_len, double *coef,
+             int coef_len) {
     problem *h = (problem *)hp;
     int neu = h->bc == BC_NEUMANN;
     int off = neu ? 0 : h->mtop;
@@ -1114,6 +1120,7 @@ int or_solve(void *hp, const double *b_orig, double *x_orig, double tol, int max
         double pq = dot(m, p, q);
         if (!(pq > 0.0)) { status = OR_EBREAKDOWN; break; }
         double alpha = rz / pq;
+        if (coef && 2 * k < coef_len) coef[2 * k] = alpha;
         for (int i = 0; i < m; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
         double rn = sqrt(dot(m, r, r));
         *iters = k + 1;
@@ -1131,6 +1138,7 @@ int or_solve(void *hp, const double *b_orig, double *x_orig, double tol, int max
             beta = rzn / rz;
             rz = rzn;
         }
+        if (coef && 2 * k + 1 < coef_len) coef[2 * k + 1] = beta;
         for (int i = 0; i < m; ++i) p[i] = z[i] + beta * p[i];
         if (flexible) rz = dot(m, r, z);
     }

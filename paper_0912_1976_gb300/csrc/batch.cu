@@ -861,7 +861,7 @@ BatchWork *new_batch_work(vemg_hierarchy *h, int K, cudaStream_t s) {
 int solve_batch(vemg_hierarchy *h, int k, const double *Bin, int64_t ldb, double *Xout, int64_t ldx, double rtol,
                 int max_it, vemg_info *infos, cudaStream_t s) {
     if (k == 0) return VEMG_OK;
-    if (k > kMaxK) throw Error{VEMG_EINVAL};
+    if (k > kMaxK || h->precond == VEMG_PRECOND_NONE) throw Error{VEMG_EINVAL};
     prepare_solve(h, s);
     int K = 1;
     while (K < k) K *= 2;
@@ -1054,7 +1054,7 @@ struct vemg_engine : vemg::Engine {};
 extern "C" {
 
 int vemg_engine_create(vemg_hierarchy *h, int slots, void *stream, vemg_engine **out) {
-    if (!h || !out || slots < 1 || slots > kMaxK) return VEMG_EINVAL;
+    if (!h || !out || slots < 1 || slots > kMaxK || h->precond == VEMG_PRECOND_NONE) return VEMG_EINVAL;
     *out = nullptr;
     vemg_engine *e = new vemg_engine();
     try {

@@ -1,5 +1,7 @@
 // capi.cu -- the extern "C" entry points of libvemg (declared in include/vemg.h): argument
 // checks, the device allocator, status codes, and introspection of the hierarchy.
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -118,6 +120,73 @@ void vemg_default_options(vemg_options *o) {
 
 const char *vemg_last_error(void) { return last_cuda_error(); }
 
+int vemg_solve_coefficients(vemg_hierarchy *h, int capacity, double *alpha, double *beta, int *count) {
+    return guarded([&] {
+        if (!h || !count || capacity < 0) return VEMG_EINVAL;
+        if (!h->coef) {
+            *count = 0;
+            return VEMG_OK;
+        }
+        if (h->precision != VEMG_PREC_FP64) return VEMG_EINVAL;
+        double it = 0.0;
+        std::vector<double> c(kCoefCap);
+        VEMG_CHECK_CUDA(cudaDeviceSynchronize());
+        VEMG_CHECK_CUDA(cudaMemcpy(&it, h->scal + solve_scalar_iters(), sizeof(double), cudaMemcpyDeviceToHost));
+        VEMG_CHECK_CUDA(cudaMemcpy(c.data(), h->coef, sizeof(double) * kCoefCap, cudaMemcpyDeviceToHost));
+        int k = std::min((int)it, kCoefCap / 2);
+        *count = k;
+        if (capacity < k || (k > 0 && (!alpha || !beta))) return VEMG_EINVAL;
+        for (int j = 0; j < k; ++j) {
+            alpha[j] = c[2 * j];
+            beta[j] = j == 0 ? 0.0 : c[2 * j - 1];
+        }
+        return VEMG_OK;
+    });
+}
+
+// number of eigenvalues of the symmetric tridiagonal (d, e) below x (Sturm sequence)
+static int sturm_below(const std::vector<double> &d, const std::vector<double> &e, double x) {
+    int cnt = 0;
+    double q = 1.0;
+    for (size_t j = 0; j < d.size(); ++j) {
+        double off = j == 0 ? 0.0 : e[j - 1] * e[j - 1] / q;
+        q = (d[j] - x) - off;
+        if (q == 0.0) q = -1e-300;
+        if (q < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+int vemg_lanczos_extremes(const double *alpha, const double *beta, int count, double *lmin, double *lmax) {
+    if (!alpha || !beta || !lmin || !lmax || count < 1) return VEMG_EINVAL;
+    for (int k = 0; k < count; ++k)
+        if (!(alpha[k] > 0.0) || (k > 0 && !(beta[k] > 0.0))) return VEMG_EINVAL;
+    std::vector<double> d(count), e(count > 1 ? count - 1 : 0);
+    for (int k = 0; k < count; ++k) {
+        d[k] = 1.0 / alpha[k] + (k > 0 ? beta[k] / alpha[k - 1] : 0.0);
+        if (k + 1 < count) e[k] = std::sqrt(beta[k + 1]) / alpha[k];
+    }
+    // Gershgorin interval
+    double lo = d[0], hi = d[0];
+    for (int k = 0; k < count; ++k) {
+        double rad = (k > 0 ? std::fabs(e[k - 1]) : 0.0) + (k + 1 < count ? std::fabs(e[k]) : 0.0);
+        lo = std::min(lo, d[k] - rad);
+        hi = std::max(hi, d[k] + rad);
+    }
+    auto kth = [&](int which) {   // the eigenvalue with index `which` (0 = smallest)
+        double a = lo, b = hi;
+        for (int it = 0; it < 200 && b - a > 1e-15 * std::max(std::fabs(a), std::fabs(b)); ++it) {
+            double m = 0.5 * (a + b);
+            if (sturm_below(d, e, m) > which) b = m;
+            else a = m;
+        }
+        return 0.5 * (a + b);
+    };
+    *lmin = kth(0);
+    *lmax = kth(count - 1);
+    return VEMG_OK;
+}
+
 int vemg_selftest_barrier(int claimed_blocks, int launched_blocks, void *stream) {
     return guarded([&] { return barrier_selftest(claimed_blocks, launched_blocks, (cudaStream_t)stream); });
 }
@@ -186,17 +255,22 @@ int vemg_setup(const vemg_csr *A, const vemg_mesh *mesh, const vemg_options *opt
         if ((o.bc != VEMG_NEUMANN && o.bc != VEMG_DIRICHLET_TOP) ||
             (o.precision != VEMG_PREC_FP64 && o.precision != VEMG_PREC_FP32) || !(o.strength >= 0.0) ||
             !(o.omega_p > 0.0) || o.coarse_max < 1 || o.coarse_max > 1024 || o.max_levels < 1 ||
-            o.max_levels > kMaxLevels || o.precond < VEMG_PRECOND_ADDITIVE || o.precond > VEMG_PRECOND_SA ||
+            o.max_levels > kMaxLevels || o.precond < VEMG_PRECOND_ADDITIVE || o.precond > VEMG_PRECOND_NONE ||
             (o.precond == VEMG_PRECOND_VL_SOR && o.bc != VEMG_NEUMANN) ||
             (o.cycle != VEMG_CYCLE_PERSISTENT && o.cycle != VEMG_CYCLE_LAUNCHES && o.cycle != VEMG_CYCLE_AUTO))
             return VEMG_EINVAL;
         h = new vemg_hierarchy();
+        if (o.precond == VEMG_PRECOND_NONE) {   // plain CG: nothing to run in FP32 or persistently
+            o.precision = VEMG_PREC_FP64;
+            o.cycle = VEMG_CYCLE_LAUNCHES;
+        }
         if (o.cycle == VEMG_CYCLE_AUTO)
             o.cycle = o.precision == VEMG_PREC_FP64 ? VEMG_CYCLE_PERSISTENT : VEMG_CYCLE_LAUNCHES;
         h->opts = o;
         h->bc = o.bc;
         h->precision = o.precision;
-        h->precond = o.bc == VEMG_DIRICHLET_TOP ? VEMG_PRECOND_ADDITIVE : o.precond;
+        h->precond = (o.bc == VEMG_DIRICHLET_TOP && o.precond != VEMG_PRECOND_NONE) ? VEMG_PRECOND_ADDITIVE
+                                                                                   : o.precond;
         setup(h, A, mesh, (cudaStream_t)stream);
         prepare_solve(h, (cudaStream_t)stream);
         return VEMG_OK;

@@ -243,9 +243,11 @@ struct vemg_hierarchy {
     unsigned *ctr = nullptr;                      // arrival counters of the block reductions
     vemg::BatchWork *batch = nullptr;             // multi-right-hand-side work (batch.cu)
     vemg::Persist *persist = nullptr;             // the persistent preconditioner program (persist.cu)
+    double *coef = nullptr;                       // CG coefficients of the last solve (alpha, beta)
 };
 
 namespace vemg {
+static constexpr int kCoefCap = 8192;   // CG coefficients kept per solve: 4096 iterations
 // the preconditioner is one V-cycle of one chain (Dirichlet-top, VL_SOR, SA) rather than the two
 // branches of the additive form
 inline bool single_chain(const vemg_hierarchy *h) {
@@ -260,6 +262,7 @@ void persist_reset(vemg_hierarchy *h, cudaStream_t s);
 double persist_bytes(const vemg_hierarchy *h);
 const int *persist_err(const vemg_hierarchy *h);
 int barrier_selftest(int claimed, int launched, cudaStream_t s);
+int solve_scalar_iters();   // index of the iteration count among the solve's device scalars
 void persist_profile_reset(vemg_hierarchy *h);
 int persist_profile(vemg_hierarchy *h, int cap, int *count, int *op, int *level, int *group, double *cycles);
 // setup.cu

@@ -222,6 +222,11 @@ __global__ void k_compose(int n, const int *__restrict__ a, const int *__restric
     if (i < n) out[i] = a[off + b[i]];
 }
 
+__global__ void k_iota(int n, int *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = i;
+}
+
 void build_solve_layout(vemg_hierarchy *h, cudaStream_t s) {
     Arena &ar = h->arena;
     bool fp32 = h->precision == VEMG_PREC_FP32;
@@ -244,6 +249,16 @@ void build_solve_layout(vemg_hierarchy *h, cudaStream_t s) {
         h->ETs = build_sell(ar, h->ET, mt, h->surf.lv[0].crow, n2s, n, {0, mt}, false, false, nullptr, nullptr, nullptr, s);
         h->caller_of = ar.alloc<int>(n);
         k_compose<<<grid_for(n, 256), 256, 0, s>>>(n, h->new2old, s2n, 0, h->caller_of);
+        VEMG_CHECK_LAUNCH();
+    } else if (h->precond == VEMG_PRECOND_NONE && h->bc == VEMG_NEUMANN) {
+        // plain CG: no cycle, the unknowns in their internal order
+        h->nu = n;
+        Scratch<int> iota(n);
+        k_iota<<<grid_for(n, 256), 256, 0, s>>>(n, iota);
+        VEMG_CHECK_LAUNCH();
+        h->Aop = build_sell(ar, h->A, n, iota, iota, n, {0, n}, false, false, nullptr, nullptr, nullptr, s);
+        h->caller_of = ar.alloc<int>(n);
+        k_compose<<<grid_for(n, 256), 256, 0, s>>>(n, h->new2old, iota, 0, h->caller_of);
         VEMG_CHECK_LAUNCH();
     } else {
         // one chain whose level 0 is the operator of the unknowns (A_bar for Dirichlet-top, A for

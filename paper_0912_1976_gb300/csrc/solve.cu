@@ -267,6 +267,8 @@ enum {
 };
 enum { C_SPMV = 0, C_XR, C_Z, C_SUMB, C_PREP, C_SUMX, C_TRUE, C_COUNT };
 
+int solve_scalar_iters() { return S_ITERS; }
+
 template <int NS>
 __device__ bool finish_block(double (&acc)[NS], double *part, unsigned *counter, double (&tot)[NS]) {
     __shared__ double sh[NS][kRedThreads / 32];
@@ -324,7 +326,7 @@ static SellArgs sargs(const Sell &S) {
 // q = A p over all slices and (p, q); the last block sets alpha = rz / pq
 __global__ void __launch_bounds__(kRedThreads) k_spmv_pq(SellArgs A, const double *__restrict__ p,
                                                          double *__restrict__ q, double *sc, double *part,
-                                                         unsigned *ctr) {
+                                                         unsigned *ctr, double *coef) {
     pdl_begin();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double acc[1] = {0.0};
@@ -345,6 +347,9 @@ __global__ void __launch_bounds__(kRedThreads) k_spmv_pq(SellArgs A, const doubl
         sc[S_FLAG] = 1.0;
         sc[S_ALPHA] = 0.0;
     } else sc[S_ALPHA] = sc[S_RZ] / pq;
+    // CG coefficient history: alpha_k at 2k (k = iterations completed so far)
+    const int k = (int)sc[S_ITERS];
+    if (2 * k < kCoefCap) coef[2 * k] = sc[S_ALPHA];
 }
 
 // x += alpha p, r -= alpha q; the last block sets ||r||, the iteration count and the continuation
@@ -402,7 +407,7 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(int nu, int mtop, SellA
                                                          const double *__restrict__ r, const double *__restrict__ q,
                                                          int neumann, int flexible, int first, double inv_n,
                                                          double *sc, double *part, unsigned *ctr,
-                                                         const int *__restrict__ perr) {
+                                                         const int *__restrict__ perr, double *coef) {
     pdl_begin();
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     constexpr int stride = kRedBlocks * kRedThreads;
@@ -468,6 +473,9 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(int nu, int mtop, SellA
     sc[S_RZ] = rz;
     if (!(rz == rz) || !(beta == beta)) sc[S_FLAG] = 1.0;
     if (perr && *(const volatile int *)perr) sc[S_FLAG] = 2.0;   // the persistent cycle gave up waiting
+    // CG coefficient history: beta_k at 2k - 1 (k = iterations completed so far, k >= 1)
+    const int k = (int)sc[S_ITERS];
+    if (!first && k >= 1 && 2 * k - 1 < kCoefCap) coef[2 * k - 1] = beta;
 }
 
 // p = (z - mu) + beta p
@@ -571,7 +579,10 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
     // probes of the per-phase kernel classes time the launch-per-phase cycle
     const int pk = h->probe.kind;
     const bool persist = h->persist && pk != PROBE_SOR && pk != PROBE_SOR_FINE && pk != PROBE_RESIDUAL;
-    if (persist) {
+    const bool none = h->precond == VEMG_PRECOND_NONE;
+    if (none) {
+        // no preconditioner (plain CG): z = r, formed by k_combine below
+    } else if (persist) {
         // both branches (or the single chain) in one cooperative kernel
         {
             ProbeScope ps(PROBE_VCYCLE, persist_bytes(h), s);
@@ -589,15 +600,16 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_join, h->side));
         ys = (const XT *)S.lv[0].x;
     }
-    if (!persist) {
+    if (!persist && !none) {
         // additive smoother: one V-cycle on A_bar with the trailing part of r
         vcycle_level<XT, double>(B, 0, r + mt, (XT *)B.lv[0].x, s);
         if (two) VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
     }
-    pdl_launch(k_combine<XT>, kRedBlocks, kRedThreads, s, h->nu, mt, sargs(h->Enon), ys, (const XT *)B.lv[0].x, z, r,
+    const XT *xb = none ? (const XT *)r : (const XT *)B.lv[0].x;   // none: XT is double
+    pdl_launch(k_combine<XT>, kRedBlocks, kRedThreads, s, h->nu, mt, sargs(h->Enon), ys, xb, z, r,
                                                      h->q, neu, flex, first, 1.0 / (double)h->nu, h->scal,
                                                      h->red + 5 * kRedBlocks * C_Z, h->ctr + C_Z,
-                                                     persist ? persist_err(h) : nullptr);
+                                                     persist ? persist_err(h) : nullptr, h->coef);
     SOLVE_LAUNCHED();
 }
 
@@ -610,7 +622,7 @@ static void precond_solve_order(vemg_hierarchy *h, const double *r, double *z, i
 static void spmv_outer(vemg_hierarchy *h, const double *x, double *y, cudaStream_t s) {
     ProbeScope ps(PROBE_SPMV_A, sell_bytes(h->Aop.nnz, 8.0, h->Aop.n, 24.0), s);   // p read twice, q write
     pdl_launch(k_spmv_pq, kRedBlocks, kRedThreads, s, sargs(h->Aop), x, y, h->scal, h->red + 5 * kRedBlocks * C_SPMV,
-                                                 h->ctr + C_SPMV);
+                                                 h->ctr + C_SPMV, h->coef);
     SOLVE_LAUNCHED();
 }
 
@@ -794,6 +806,7 @@ void prepare_solve(vemg_hierarchy *h, cudaStream_t s) {
     h->red = ar.alloc<double>(5 * kRedBlocks * C_COUNT);
     h->scal = ar.alloc<double>(S_COUNT);
     h->ctr = ar.alloc<unsigned>(C_COUNT);
+    h->coef = ar.alloc<double>(kCoefCap);
     VEMG_CHECK_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(unsigned) * C_COUNT, s));
     h->tops = ar.alloc<int>(h->mtop);
     // caller ids of the top nodes (written as 0 by Dirichlet-top solves)
@@ -802,7 +815,7 @@ void prepare_solve(vemg_hierarchy *h, cudaStream_t s) {
     VEMG_CHECK_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     VEMG_CHECK_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
-    if (h->opts.cycle == VEMG_CYCLE_PERSISTENT) build_persist(h, s);
+    if (h->opts.cycle == VEMG_CYCLE_PERSISTENT && h->precond != VEMG_PRECOND_NONE) build_persist(h, s);
 }
 
 int solve(vemg_hierarchy *h, const double *b_in, double *x_out, double rtol, int max_it, vemg_info *info,

@@ -90,9 +90,21 @@ def _tet_volumes6(xyz: np.ndarray, tets: np.ndarray) -> np.ndarray:
     return np.einsum("ij,ij->i", d1, np.cross(d2, d3))
 
 
+def _cluster_map(t: np.ndarray, c: float):
+    """Monotone map of [0, 1] onto itself (for 0 <= c < 1) whose slope is 1 - c at t = 1/2 and
+    1 + c at the ends: grid points crowd towards the centre. Returns (map, slope)."""
+    w = 2.0 * np.pi * t
+    return t + c * np.sin(w) / (2.0 * np.pi), 1.0 + c * np.cos(w)
+
+
 def make_mesh(nx: int, ny: int, nz: int, depth, *, z_jitter: float = 0.0,
-              xy_jitter: float = 0.0, seed: int = 0, max_passes: int = 100) -> Mesh:
+              xy_jitter: float = 0.0, seed: int = 0, max_passes: int = 100, cluster: float = 0.0) -> Mesh:
     """Extruded hex mesh of the unit square x [-H(x,y), 0], each hex split into 6 Kuhn tets.
+
+    cluster: 0 <= c < 1. The grid coordinates i/nx, j/ny and the layer fraction k/nz pass through
+      a monotone map whose spacing shrinks by a factor (1 - c)/(1 + c) from the edges to the
+      centre: a multiscale mesh with small elements at the centre of the domain (the clustered
+      mesh of section 6). Jitter amplitudes below are scaled by the local spacing.
 
     z_jitter: nodes strictly between top and floor move vertically by
       U(-z_jitter, z_jitter) times the local layer thickness H(x, y) / nz.
@@ -109,8 +121,11 @@ def make_mesh(nx: int, ny: int, nz: int, depth, *, z_jitter: float = 0.0,
     col = nid // (nz + 1)
     i = col % (nx + 1)
     j = col // (nx + 1)
-    x0 = i.astype(np.float64) / nx
-    y0 = j.astype(np.float64) / ny
+    if not (0.0 <= cluster < 1.0):
+        raise ValueError("cluster must lie in [0, 1)")
+    x0, sx = _cluster_map(i.astype(np.float64) / nx, cluster)
+    y0, sy = _cluster_map(j.astype(np.float64) / ny, cluster)
+    zeta, sz = _cluster_map(k.astype(np.float64) / nz, cluster)
 
     tags = np.zeros(n, dtype=np.uint8)
     tags[k == 0] |= TAG_TOP
@@ -127,11 +142,11 @@ def make_mesh(nx: int, ny: int, nz: int, depth, *, z_jitter: float = 0.0,
     jz = _uniform_pm1(rng, n)
 
     def coords(jx, jy, jz):
-        x = np.where(movable_xy, x0 + xy_jitter * jx * (1.0 / nx), x0)
-        y = np.where(movable_xy, y0 + xy_jitter * jy * (1.0 / ny), y0)
+        x = np.where(movable_xy, x0 + xy_jitter * jx * (sx / nx), x0)
+        y = np.where(movable_xy, y0 + xy_jitter * jy * (sy / ny), y0)
         h = depth(x, y)
-        z = -h * (k.astype(np.float64) / nz)
-        z = np.where(movable_z, z + z_jitter * jz * (h / nz), z)
+        z = -h * zeta
+        z = np.where(movable_z, z + z_jitter * jz * (h * sz / nz), z)
         z = np.where(k == 0, 0.0, z)
         return np.stack([x, y, z], axis=1)
 
@@ -221,6 +236,10 @@ WORKLOADS = {
     # 384x384x24, H = 1e-3 (1 + 0.5 sin sin), z-jitter 0.3, 64 right-hand sides
     "zjit384x64": dict(nx=384, ny=384, nz=24, depth=("sines", 1e-3), z_jitter=0.3, xy_jitter=0.0,
                        seed=4000, rhs="normal", nrhs=64, rtol=1e-8),
+    # multiscale stand-in for the clustered mesh of section 6: 128x128x24 with spacing 19x finer at
+    # the centre than at the edges (horizontally and vertically), z-jitter 0.3, H = 1e-3 (...)
+    "cluster128": dict(nx=128, ny=128, nz=24, depth=("sines", 1e-3), z_jitter=0.3, xy_jitter=0.0,
+                       cluster=0.9, seed=6000, rhs="normal", rtol=1e-8),
 }
 
 
@@ -233,7 +252,7 @@ def make_workload_mesh(name: str, **over) -> Mesh:
     w = dict(WORKLOADS[name])
     w.update(over)
     return make_mesh(w["nx"], w["ny"], w["nz"], depth_fn(w["depth"]), z_jitter=w["z_jitter"],
-                     xy_jitter=w["xy_jitter"], seed=w["seed"])
+                     xy_jitter=w["xy_jitter"], seed=w["seed"], cluster=w.get("cluster", 0.0))
 
 
 def scale_depth(mesh: Mesh, factor: float) -> Mesh:

@@ -18,7 +18,7 @@ VEMG_OK, VEMG_EINVAL, VEMG_EMESH, VEMG_ENOMEM, VEMG_ENOTCONV, VEMG_EBREAKDOWN, V
     VEMG_EINTERNAL = range(9)
 VEMG_NEUMANN, VEMG_DIRICHLET_TOP = 0, 1
 VEMG_PREC_FP64, VEMG_PREC_FP32 = 0, 1
-VEMG_PRECOND_ADDITIVE, VEMG_PRECOND_VL_SOR, VEMG_PRECOND_SA = 0, 1, 2
+VEMG_PRECOND_ADDITIVE, VEMG_PRECOND_VL_SOR, VEMG_PRECOND_SA, VEMG_PRECOND_NONE = 0, 1, 2, 3
 VEMG_CYCLE_PERSISTENT, VEMG_CYCLE_LAUNCHES, VEMG_CYCLE_AUTO = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ENOTCONV", 5: "EBREAKDOWN",
                 6: "ETIMEOUT", 7: "ECUDA", 8: "EINTERNAL"}
@@ -66,6 +66,8 @@ PROTOTYPES = {
     "vemg_default_options": (None, [C.POINTER(vemg_options)]),
     "vemg_last_error": (C.c_char_p, []),
     "vemg_selftest_barrier": (C.c_int, [C.c_int, C.c_int, _VP]),
+    "vemg_solve_coefficients": (C.c_int, [_VP, C.c_int, _DP, _DP, C.POINTER(C.c_int)]),
+    "vemg_lanczos_extremes": (C.c_int, [_DP, _DP, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "vemg_assemble": (C.c_int, [C.POINTER(vemg_mesh), C.POINTER(vemg_csr), _VP]),
     "vemg_load": (C.c_int, [C.POINTER(vemg_mesh), _DP, _DP, _VP]),
     "vemg_csr_free": (None, [C.POINTER(vemg_csr)]),
@@ -305,6 +307,27 @@ def vemg_hierarchy_bytes(h: Hierarchy) -> int:
 def vemg_selftest_barrier(claimed_blocks: int, launched_blocks: int, stream=None) -> int:
     """Status of one bounded grid-barrier wait: VEMG_OK or VEMG_ETIMEOUT (returned, not raised)."""
     return lib().vemg_selftest_barrier(claimed_blocks, launched_blocks, _stream(stream))
+
+
+def vemg_solve_coefficients(h: Hierarchy):
+    """(alpha, beta) numpy arrays of the last vemg_solve on h (FP64 V-cycles)."""
+    cnt = C.c_int(0)
+    lib().vemg_solve_coefficients(h.h, 0, None, None, C.byref(cnt))
+    n = cnt.value
+    a, b = np.zeros(max(n, 1)), np.zeros(max(n, 1))
+    _check(lib().vemg_solve_coefficients(h.h, n, C.c_void_p(a.ctypes.data), C.c_void_p(b.ctypes.data),
+                                         C.byref(cnt)), "vemg_solve_coefficients")
+    return a[:n], b[:n]
+
+
+def vemg_lanczos_extremes(alpha, beta):
+    """(lambda_min, lambda_max) of the Lanczos tridiagonal of CG coefficients."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    lo, hi = C.c_double(), C.c_double()
+    _check(lib().vemg_lanczos_extremes(C.c_void_p(a.ctypes.data), C.c_void_p(b.ctypes.data), len(a), C.byref(lo),
+                                       C.byref(hi)), "vemg_lanczos_extremes")
+    return lo.value, hi.value
 
 
 def vemg_strerror(code: int) -> str:

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 # orders, so each result differs by a few ulps; the Krylov iteration and the coarse solves amplify
 # such differences by the conditioning of A, which grows like eps^-2 (section 4). 1e-9 holds for
 # eps >= 1e-3; the eps = 1e-4 mesh is 100x worse conditioned, so its bound is 1e-7.
-XTOL = {"box16": 1e-9, "zjit24": 1e-9, "xyjit20": 1e-7, "zjit64": 1e-9}
+XTOL = {"box16": 1e-9, "zjit24": 1e-9, "xyjit20": 1e-7, "zjit64": 1e-9, "clust32": 1e-9}
 
 CASES = {
     # the 16x16x8 thin box with flat depth 0.01 (no jitter)
@@ -31,6 +31,8 @@ CASES = {
     "xyjit20": lambda: I.make_mesh(20, 20, 8, I.depth_sines(1e-4), z_jitter=0.3, xy_jitter=0.2, seed=8),
     # several thread blocks per kernel and a ragged tail, four multigrid levels
     "zjit64": lambda: I.make_mesh(64, 61, 32, I.depth_sines(1e-3), z_jitter=0.3, seed=9),
+    # multiscale: spacing 19x finer at the centre than at the edges
+    "clust32": lambda: I.make_mesh(32, 30, 12, I.depth_sines(1e-3), z_jitter=0.3, seed=10, cluster=0.9),
 }
 
 _cache = {}
@@ -138,7 +140,7 @@ def test_fixed_iteration_iterates_match(name):
         assert abs(ig["relres"] - ro["relres"]) <= XTOL[name]
 
 
-@pytest.mark.parametrize("name", ["box16", "zjit24", "zjit64"])
+@pytest.mark.parametrize("name", ["box16", "zjit24", "zjit64", "clust32"])
 def test_converged_solve_matches(name):
     m, om, vm, A, h = _setup(name)
     if name == "box16":

@@ -506,3 +506,109 @@ def test_section6_sa_degrades_with_aspect_ratio_vl_does_not():
     assert its[O.PC_SA][-1] > 5 * its[O.PC_SA][0], its
     # the multiplicative VL+SOR cycle needs fewer iterations than the additive one
     assert all(v < a for v, a in zip(its[O.PC_VL_SOR], its[O.PC_ADDITIVE])), its
+
+
+# --------------------------------------------------------------------------------------------
+# the clustered (multiscale) mesh of section 6
+
+def test_cluster_map_is_identity_at_zero_and_grades_spacing():
+    a = I.make_mesh(6, 5, 4, I.depth_sines(0.01), z_jitter=0.3, seed=5)
+    b = I.make_mesh(6, 5, 4, I.depth_sines(0.01), z_jitter=0.3, seed=5, cluster=0.0)
+    assert np.array_equal(a.xyz.view(np.uint64), b.xyz.view(np.uint64))
+    c = 0.9
+    m = I.make_mesh(40, 40, 12, I.depth_flat(1.0), seed=5, cluster=c)
+    top = m.xyz[m.tags & I.TAG_TOP != 0]
+    xs = np.unique(np.round(top[:, 0], 14))
+    dx = np.diff(xs)
+    # spacing (1 - c)/n at the centre, (1 + c)/n at the edges, to second order in 1/n
+    assert abs(dx.min() * 40 - (1 - c)) < 0.02 and abs(dx.max() * 40 - (1 + c)) < 0.02
+    assert xs[0] == 0.0 and xs[-1] == 1.0
+    vol = np.linalg.det(np.stack([m.xyz[m.tets[:, k]] - m.xyz[m.tets[:, 0]] for k in (1, 2, 3)], axis=1))
+    assert (vol > 0).all() and vol.max() / vol.min() > 1e3
+
+
+def test_section6_clustered_mesh_sa_degrades_lumped_forms_do_not():
+    """Section 6, clustered mesh: smoothed aggregation slows down as eps shrinks, while both
+    vertically lumped forms reach an eps-independent rate for small eps."""
+    its = {pc: [] for pc in (O.PC_ADDITIVE, O.PC_VL_SOR, O.PC_SA)}
+    for eps in [1e-1, 1e-3, 1e-4]:
+        m = I.make_mesh(48, 48, 12, I.depth_sines(eps), z_jitter=0.3, seed=8, cluster=0.9)
+        for pc in its:
+            P = O.Problem(m, precond=pc)
+            r = P.solve(I.normal_loads(P.n, 2), tol=1e-8, maxit=3000)
+            assert r["status"] == "OK"
+            its[pc].append(r["iters"])
+    assert its[O.PC_SA][1] > 2 * its[O.PC_SA][0], its
+    for pc in (O.PC_ADDITIVE, O.PC_VL_SOR):
+        a, b = its[pc][1], its[pc][2]
+        assert abs(a - b) <= 0.2 * min(a, b), its
+
+
+# --------------------------------------------------------------------------------------------
+# spectrum (section 4): Lanczos tridiagonal from the CG coefficients
+
+def _lanczos_T(alpha, beta):
+    k = len(alpha)
+    d = np.array([1.0 / alpha[j] + (beta[j] / alpha[j - 1] if j > 0 else 0.0) for j in range(k)])
+    e = np.array([np.sqrt(beta[j + 1]) / alpha[j] for j in range(k - 1)])
+    return np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+
+
+def test_cg_coefficients_give_the_spectrum_of_A_and_of_the_preconditioned_operator():
+    """Plain CG on A (Neumann, mean-zero right-hand side) is Lanczos on A restricted to the
+    complement of the constants; PCG is Lanczos on M^-1 A. Their extreme Ritz values converge
+    to the extreme eigenvalues computed densely."""
+    m = _mesh(6, 3, h0=0.05, zj=0.3)
+    b = I.normal_loads(m.xyz.shape[0], 7)
+    # A on the complement of the constants
+    P0 = O.Problem(m, precond=O.PC_NONE)
+    A = P0.csr("A").toarray()
+    n = A.shape[0]
+    Q = np.linalg.qr(np.eye(n) - 1.0 / n)[0][:, : n - 1]
+    w = np.linalg.eigvalsh(Q.T @ A @ Q)
+    r = P0.solve(b, tol=1e-12, maxit=5000)   # converged: the extreme Ritz values have converged too
+    assert r["status"] == "OK"
+    lam = np.linalg.eigvalsh(_lanczos_T(r["alpha"], r["beta"]))
+    assert abs(lam[-1] - w[-1]) <= 1e-8 * w[-1]
+    assert abs(lam[0] - w[0]) <= 1e-6 * w[0]
+    # M^-1 A for the additive preconditioner, on the same complement
+    P = O.Problem(m, coarse_max=40)
+    Mz = np.stack([P.precond(e) for e in np.eye(n)], axis=1)
+    Mz = 0.5 * (Mz + Mz.T)
+    S = Q.T @ Mz @ Q
+    L = np.linalg.cholesky(S)
+    wm = np.linalg.eigvalsh(L.T @ (Q.T @ A @ Q) @ L)   # similar to M^-1 A on the complement
+    rp = P.solve(b, tol=1e-12, maxit=400)
+    assert rp["status"] == "OK"
+    lp = np.linalg.eigvalsh(_lanczos_T(rp["alpha"], rp["beta"]))
+    # PCG stops after ~30 iterations: its extreme Ritz values are converged to ~1e-6
+    assert abs(lp[-1] - wm[-1]) <= 1e-5 * wm[-1]
+    assert abs(lp[0] - wm[0]) <= 1e-5 * wm[0]
+
+
+def test_library_lanczos_extremes_match_numpy():
+    from paper_0912_1976_gb300 import vemg as V
+    rng = np.random.default_rng(3)
+    for k in (1, 2, 7, 40):
+        alpha = rng.uniform(0.1, 2.0, k)
+        beta = np.concatenate([[0.0], rng.uniform(0.01, 1.5, k - 1)])
+        w = np.linalg.eigvalsh(_lanczos_T(alpha, beta))
+        lo, hi = V.vemg_lanczos_extremes(alpha, beta)
+        assert abs(lo - w[0]) <= 1e-12 * abs(w[-1]) and abs(hi - w[-1]) <= 1e-12 * abs(w[-1])
+
+
+def test_section4_preconditioned_condition_number_independent_of_eps():
+    """Section 4 / 6.2: Cond(A) grows like eps^-2, while the condition number of the preconditioned
+    operator (Lanczos estimate from the PCG coefficients) stays bounded."""
+    ka, km = [], []
+    for eps in [1e-2, 1e-3, 1e-4]:
+        m = _mesh(16, 8, h0=eps, zj=0.3, seed=4)
+        b = I.normal_loads(m.xyz.shape[0], 2)
+        r = O.Problem(m, precond=O.PC_NONE).solve(b, tol=1e-10, maxit=4000)
+        la = np.linalg.eigvalsh(_lanczos_T(r["alpha"], r["beta"]))
+        ka.append(la[-1] / la[0])
+        rp = O.Problem(m).solve(b, tol=1e-8, maxit=400)   # above the eps = 1e-4 round-off floor
+        lm = np.linalg.eigvalsh(_lanczos_T(rp["alpha"], rp["beta"]))
+        km.append(lm[-1] / lm[0])
+    assert ka[1] > 30 * ka[0] and ka[2] > 30 * ka[1], ka
+    assert max(km) <= 1.5 * min(km), km
