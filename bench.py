@@ -60,6 +60,8 @@ def parse():
                     help="profiling case NXxNYxNZ (z-jitter 0.3, eps 1e-3): two untimed solves, then exit")
     ap.add_argument("--spectrum", action="store_true",
                     help="the section 4 study: condition estimates of A and M^-1 A over eps (not a timing run)")
+    ap.add_argument("--phases", action="store_true",
+                    help="with --case: per-phase profile of the persistent preconditioner kernel")
     ap.add_argument("--stream-path", action="store_true",
                     help="with --case: launch the solve's kernels on the stream, not from CUDA graphs")
     ap.add_argument("--rhs", type=int, default=0,
@@ -369,6 +371,37 @@ def run_serve(args):
     return 0
 
 
+def case_phases(args, m, h, V, torch):
+    """Per-phase profile of the persistent preconditioner kernel over one solve (after one warm-up
+    solve): for each (group, level, kind) the phases and their summed critical-path time."""
+    from paper_0912_1976_gb300 import inputs as I
+    b = torch.from_numpy(I.normal_loads(m.n, 5)).cuda()
+    V.vemg_solve(h, b, rtol=RTOL)
+    V.vemg_probe(h, V.VEMG_PROBE_VCYCLE)
+    _, info = V.vemg_solve(h, b, rtol=RTOL)
+    r = V.vemg_probe_read(h)
+    ph = V.vemg_probe_phases(h)
+    V.vemg_probe(h, V.VEMG_PROBE_NONE)
+    if not ph:
+        print(json.dumps({"case": args.case, "phases": None, "note": "no persistent program (cycle is launches)"}))
+        return 0
+    mhz = float(os.environ.get("VEMG_SM_MHZ", "2070"))
+    napp = max(r["launches"], 1)
+    agg = {}
+    for p in ph:
+        k = (p["group"], p["level"], p["op"])
+        a = agg.setdefault(k, [0, 0.0])
+        a[0] += 1
+        a[1] += p["cycles"]
+    rows = [{"group": g, "level": l, "op": op, "phases": c, "us_per_application": cyc / mhz / napp}
+            for (g, l, op), (c, cyc) in agg.items()]
+    print(json.dumps({"case": args.case, "precision": args.precision, "iters": info["iters"],
+                      "applications": napp, "ms_per_application": r["ms"] / napp,
+                      "algorithmic_gb_per_s": r["bytes"] / (r["ms"] / 1e3) / 1e9, "sm_mhz_assumed": mhz,
+                      "rows": rows}))
+    return 0
+
+
 def run_case(args):
     """A small case for ncu captures: build the mesh, set up, run two solves."""
     import torch
@@ -381,19 +414,28 @@ def run_case(args):
     prec = V.VEMG_PREC_FP64 if args.precision == "fp64" else V.VEMG_PREC_FP32
     h = V.vemg_setup(A, vm, V.vemg_default_options(precision=prec, precond=PRECONDS[args.precond],
                                                    cycle=CYCLES[args.cycle]))
+    if args.phases:
+        return case_phases(args, m, h, V, torch)
     kr = max(args.rhs, 1)
     if args.stream_path:
         # the same kernels launched on the stream instead of from graphs (profilers cannot see
         # into graphs with conditional nodes)
         V.vemg_probe(h, V.VEMG_PROBE_VCYCLE)
+    # the second solve runs inside the NVTX range "solve" (ncu --nvtx --nvtx-include "solve/")
     if kr == 1:
         b = torch.from_numpy(I.normal_loads(m.n, 5)).cuda()
-        for _ in range(2):
+        for j in range(2):
+            if j == 1:
+                torch.cuda.nvtx.range_push("solve")
             _, info = V.vemg_solve(h, b, rtol=RTOL)
+        torch.cuda.nvtx.range_pop()
     else:
         B = torch.from_numpy(I.normal_loads(m.n, 5, k=kr)).cuda()
-        for _ in range(2):
+        for j in range(2):
+            if j == 1:
+                torch.cuda.nvtx.range_push("solve")
             _, infos = V.vemg_solve_batch(h, B, rtol=RTOL)
+        torch.cuda.nvtx.range_pop()
         info = infos[0]
     torch.cuda.synchronize()
     print(json.dumps({"case": args.case, "n": m.n, "precision": args.precision, "rhs": kr, "info": info}))

@@ -185,6 +185,9 @@ struct SChain {
     bool direct = false, singular = false, fp32 = false, is_bar = false;
     int nc = 0;
     double *G = nullptr;           // coarsest dense inverse in solve order
+    // the coarse tail (levels tail_level.. as one single-CTA kernel, persist.cu); -1: none
+    int tail_level = -1, tail_n = 0;
+    const void *tail = nullptr;
 };
 
 struct Chain {
@@ -264,6 +267,8 @@ const int *persist_err(const vemg_hierarchy *h);
 int barrier_selftest(int claimed, int launched, cudaStream_t s);
 int solve_scalar_iters();   // index of the iteration count among the solve's device scalars
 void persist_profile_reset(vemg_hierarchy *h);
+void build_tails(vemg_hierarchy *h, cudaStream_t s);
+void launch_tail(const SChain &C, cudaStream_t s);
 int persist_profile(vemg_hierarchy *h, int cap, int *count, int *op, int *level, int *group, double *cycles);
 // setup.cu
 void assemble(const vemg_mesh *mesh, vemg_csr *A_out, cudaStream_t s);

@@ -218,15 +218,17 @@ __device__ __forceinline__ void sell_row_op(const PPhase &p, const double *__res
     }
 }
 
-template <class XT>
+// PRE: the warp's first slice of the phase was prefetched into `pre` (the grid kernel); the
+// single-CTA tail kernel runs without prefetch
+template <class XT, bool PRE>
 __device__ void run_phase(const PPhase &p, const double *__restrict__ r, int gw, int nw, int lane,
                           const Pre<XT> &pre) {
     if (sell_op<XT>(p.op)) {
         int s = p.s0 + gw;
-        if (s < p.s1 && pre.s == s) {
+        if (PRE && s < p.s1 && pre.s == s) {
             sell_row_op<XT>(p, r, pre.i, pre.o, pre.w, &pre);
             s += nw;
-        } else if (s < p.s1) {
+        } else if (PRE && s < p.s1) {
             // no prefetched row for this lane (a short slice): nothing to do in this slice
             s += nw;
         }
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(kPThreads, 3) k_precond_persistent(const PPhas
         const bool more = k + 1 < G.w;
         if (more && threadIdx.x < kPhaseWords)
             ((int *)&sp[cur ^ 1])[threadIdx.x] = __ldg((const int *)(phases + k + 1) + threadIdx.x);
-        run_phase<XT>(sp[cur], r, gw, nw, lane, pre);
+        run_phase<XT, true>(sp[cur], r, gw, nw, lane, pre);
         if (!more) {
             if (timer) atomicAdd(cycles + k, (unsigned long long)(clock64() - t0));
             break;
@@ -323,6 +325,28 @@ __global__ void __launch_bounds__(kPThreads, 3) k_precond_persistent(const PPhas
             atomicAdd(cycles + k, (unsigned long long)(t1 - t0));
             t0 = t1;
         }
+    }
+}
+
+// The coarse tail of one chain (every level from a small one down, and back up) in one CTA: the
+// phases are separated by __syncthreads() instead of kernel boundaries. Launched on the stream of
+// the launch-per-phase cycle in place of the tail's dozens of small dependent launches. (A
+// thread-block cluster of 8 CTAs with the hardware cluster barrier, tried for larger tails, was
+// slower than the launches it replaced.)
+static constexpr int kTailThreads = 1024;
+
+template <class XT>
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const PPhase *__restrict__ phases, int nphases) {
+    pdl_begin();
+    __shared__ PPhase sp;
+    const int gw = (int)(threadIdx.x >> 5), nw = kTailThreads / 32, lane = threadIdx.x & 31;
+    Pre<XT> none;
+    none.s = -1;
+    for (int k = 0; k < nphases; ++k) {
+        if (threadIdx.x < kPhaseWords) ((int *)&sp)[threadIdx.x] = __ldg((const int *)(phases + k) + threadIdx.x);
+        __syncthreads();
+        run_phase<XT, false>(sp, nullptr, gw, nw, lane, none);
+        __syncthreads();   // the phase's writes are visible to the CTA; sp may be overwritten
     }
 }
 
@@ -553,6 +577,47 @@ void build_persist(vemg_hierarchy *h, cudaStream_t s) {
         throw;
     }
     h->persist = P;
+}
+
+// Coarse tails: the first level below the finest with at most kTailRows rows starts a tail. A
+// colour of such a level has at most ~1,000 rows, about one row per thread of the tail CTA, so a
+// phase costs one memory round trip plus a CTA barrier instead of a kernel launch. One SM's
+// bandwidth bounds the size: with 32,768 rows the tail was slower than the launches.
+static constexpr int kTailRows = 12288;
+
+static void build_tail(Arena &ar, SChain &C, bool fp32, cudaStream_t s) {
+    C.tail_level = -1;
+    int l0 = -1;
+    for (int l = 1; l < C.nlev; ++l)
+        if (C.lv[l].n <= kTailRows) {
+            l0 = l;
+            break;
+        }
+    if (l0 < 0) return;
+    Builder B(ar, s);
+    B.xs = fp32 ? 4 : 8;
+    B.vcycle(C, l0, C.lv[l0].b, -1, C.lv[l0].x);
+    PPhase *d = ar.alloc<PPhase>((int)B.ph.size());
+    VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+    VEMG_CHECK_CUDA(cudaMemcpy(d, B.ph.data(), sizeof(PPhase) * B.ph.size(), cudaMemcpyHostToDevice));
+    C.tail = d;
+    C.tail_n = (int)B.ph.size();
+    C.tail_level = l0;
+}
+
+void build_tails(vemg_hierarchy *h, cudaStream_t s) {
+    const bool fp32 = h->precision == VEMG_PREC_FP32;
+    if (h->precond == VEMG_PRECOND_NONE) return;
+    if (!single_chain(h)) build_tail(h->arena, h->ssurf, fp32, s);
+    build_tail(h->arena, h->sbar, fp32, s);
+}
+
+void launch_tail(const SChain &C, cudaStream_t s) {
+    const PPhase *ph = (const PPhase *)C.tail;
+    if (C.fp32)
+        pdl_launch(k_tail<float>, 1, kTailThreads, s, ph, C.tail_n);
+    else
+        pdl_launch(k_tail<double>, 1, kTailThreads, s, ph, C.tail_n);
 }
 
 void release_persist(vemg_hierarchy *h) {

@@ -237,6 +237,13 @@ template <class XT, class BT>
 static void vcycle_level(const SChain &C, int l, const BT *b, XT *x, cudaStream_t s) {
     const SLevel &L = C.lv[l];
     const bool fine = C.is_bar && l == 0;
+    if (l > 0 && l == C.tail_level) {
+        // the coarse tail: every level from here down and back up in one single-CTA kernel
+        // (its phases read b and write x in this level's own buffers)
+        launch_tail(C, s);
+        SOLVE_LAUNCHED();
+        return;
+    }
     if (l == C.nlev - 1) {
         if (C.direct) {
             pdl_launch(k_dense_mv<XT, BT>, grid_for(C.nc, 8), 256, s, C.nc, C.G, b, x);
@@ -816,6 +823,7 @@ void prepare_solve(vemg_hierarchy *h, cudaStream_t s) {
     VEMG_CHECK_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
     if (h->opts.cycle == VEMG_CYCLE_PERSISTENT && h->precond != VEMG_PRECOND_NONE) build_persist(h, s);
+    build_tails(h, s);
 }
 
 int solve(vemg_hierarchy *h, const double *b_in, double *x_out, double rtol, int max_it, vemg_info *info,
