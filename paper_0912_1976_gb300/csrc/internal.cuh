@@ -237,6 +237,7 @@ struct vemg_hierarchy {
     int *tops = nullptr;                          // caller ids of the top nodes
     vemg::Sell Aop;                               // outer operator, FP64, diagonal included
     vemg::Sell Enon;                              // E~ rows of non-top nodes (Neumann)
+    float *Enon_vf = nullptr;                     // FP32 copy of its values (FP32 V-cycles)
     vemg::Sell ETs;                               // E~^T (surface rows)
     vemg::SChain ssurf, sbar;
     // CUDA graphs of the solve (built on the first solve)

@@ -222,6 +222,11 @@ __global__ void k_compose(int n, const int *__restrict__ a, const int *__restric
     if (i < n) out[i] = a[off + b[i]];
 }
 
+__global__ void k_to_float(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
 __global__ void k_iota(int n, int *out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = i;
@@ -247,6 +252,13 @@ void build_solve_layout(vemg_hierarchy *h, cudaStream_t s) {
         h->Enon = build_sell(ar, h->E, n - mt, s2n.p + mt, surf_inv, mt, {0, n - mt}, false, false, nullptr, nullptr,
                              nullptr, s);
         h->ETs = build_sell(ar, h->ET, mt, h->surf.lv[0].crow, n2s, n, {0, mt}, false, false, nullptr, nullptr, nullptr, s);
+        if (fp32 && h->Enon.padded > 0) {
+            // z = E~ y_s + x_bar is formed in FP32 when the V-cycles are FP32 (one conversion per row)
+            h->Enon_vf = ar.alloc<float>(h->Enon.padded);
+            k_to_float<<<grid_for(h->Enon.padded, 256), 256, 0, s>>>(h->Enon.padded, (const double *)h->Enon.v,
+                                                                      h->Enon_vf);
+            VEMG_CHECK_LAUNCH();
+        }
         h->caller_of = ar.alloc<int>(n);
         k_compose<<<grid_for(n, 256), 256, 0, s>>>(n, h->new2old, s2n, 0, h->caller_of);
         VEMG_CHECK_LAUNCH();

@@ -17,6 +17,8 @@
 
 #include <algorithm>
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace vemg {
@@ -409,29 +411,36 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(int n, const double *
 // The last block sets mu (mean of z), rz = (r, z - mu) and beta: first direction 0, CG
 // rz'/rz, FCG -(z - mu, q) / (p, q).
 template <class XT>
-__global__ void __launch_bounds__(kRedThreads) k_combine(int nu, int mtop, SellArgs E, const XT *__restrict__ ys,
-                                                         const XT *__restrict__ xb, double *__restrict__ z,
-                                                         const double *__restrict__ r, const double *__restrict__ q,
-                                                         int neumann, int flexible, int first, double inv_n,
-                                                         double *sc, double *part, unsigned *ctr,
-                                                         const int *__restrict__ perr, double *coef) {
+__global__ void __launch_bounds__(kRedThreads) k_combine(int nu, int mtop, SellArgs E, const float *__restrict__ evf,
+                                                         const XT *__restrict__ ys, const XT *__restrict__ xb,
+                                                         double *__restrict__ z, const double *__restrict__ r,
+                                                         const double *__restrict__ q, int neumann, int flexible,
+                                                         int first, double inv_n, double *sc, double *part,
+                                                         unsigned *ctr, const int *__restrict__ perr, double *coef) {
     pdl_begin();
+    // FP32 V-cycles with an FP32 copy of E~ (evf): z_i = x_bar_i + sum_k e_k y_s(c_k) is formed in
+    // FP32 and converted once (FP64 instructions are scarce on this GPU); otherwise in FP64
+    using ZT = typename std::conditional<std::is_same<XT, float>::value, float, double>::type;
+    const bool lowz = std::is_same<XT, float>::value && evf != nullptr;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     constexpr int stride = kRedBlocks * kRedThreads;
     const bool dots_q = flexible && !first;
     for (int i0 = blockIdx.x * kRedThreads + threadIdx.x; i0 < nu; i0 += kRows * stride) {
         double zv[kRows], rv[kRows], qv[kRows];
+        ZT zl[kRows];
         // loads of every row first (the E~ row entries, x_bar, r, q), then the gathers of y_s
         int ec[kRows][kEmax];
         double ev[kRows][kEmax];
+        ZT el[kRows][kEmax];
 #pragma unroll
         for (int u = 0; u < kRows; ++u) {
             int i = i0 + u * stride;
             zv[u] = 0.0;
+            zl[u] = (ZT)0;
             rv[u] = 0.0;
             qv[u] = 0.0;
 #pragma unroll
-            for (int k = 0; k < kEmax; ++k) { ec[u][k] = -1; ev[u][k] = 0.0; }
+            for (int k = 0; k < kEmax; ++k) { ec[u][k] = -1; ev[u][k] = 0.0; el[u][k] = (ZT)0; }
             if (i >= nu) continue;
             rv[u] = r[i];
             if (dots_q) qv[u] = q[i];
@@ -439,11 +448,18 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(int nu, int mtop, SellA
             if (mtop == 0) { zv[u] = (double)xb[i]; continue; }
             int qq = i - mtop, sl = qq >> 5, ln = qq & 31;
             int o = E.off[sl] + ln, w = E.width[sl];
-            zv[u] = (double)xb[qq];
+            if (lowz) zl[u] = (ZT)xb[qq];
+            else zv[u] = (double)xb[qq];
             if (w <= kEmax) {
 #pragma unroll
                 for (int k = 0; k < kEmax; ++k)
-                    if (k < w) { ec[u][k] = __ldg(E.col + o + 32 * k); ev[u][k] = __ldg(E.v + o + 32 * k); }
+                    if (k < w) {
+                        ec[u][k] = __ldg(E.col + o + 32 * k);
+                        if (lowz) el[u][k] = (ZT)__ldg(evf + o + 32 * k);
+                        else ev[u][k] = __ldg(E.v + o + 32 * k);
+                    }
+            } else if (lowz) {
+                zl[u] += (ZT)sell_row<float, XT, float>(E.col, evf, o, w, ys, -1);
             } else {
                 zv[u] += sell_row<double, XT, double>(E.col, E.v, o, w, ys, -1);
             }
@@ -452,11 +468,20 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(int nu, int mtop, SellA
         for (int u = 0; u < kRows; ++u) {
             int i = i0 + u * stride;
             if (i >= nu) continue;
-            double zi = zv[u];
-            if (i < mtop) zi = (double)ys[i];
+            double zi;
+            if (lowz && i >= mtop && mtop > 0) {
+                ZT zf = zl[u];
 #pragma unroll
-            for (int k = 0; k < kEmax; ++k)
-                if (ec[u][k] >= 0) zi += ev[u][k] * (double)ys[ec[u][k]];
+                for (int k = 0; k < kEmax; ++k)
+                    if (ec[u][k] >= 0) zf += el[u][k] * (ZT)ys[ec[u][k]];
+                zi = (double)zf;
+            } else {
+                zi = zv[u];
+                if (i < mtop) zi = (double)ys[i];
+#pragma unroll
+                for (int k = 0; k < kEmax; ++k)
+                    if (ec[u][k] >= 0) zi += ev[u][k] * (double)ys[ec[u][k]];
+            }
             z[i] = zi;
             acc[0] += zi;
             acc[1] += rv[u] * zi;
@@ -613,7 +638,7 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
         if (two) VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
     }
     const XT *xb = none ? (const XT *)r : (const XT *)B.lv[0].x;   // none: XT is double
-    pdl_launch(k_combine<XT>, kRedBlocks, kRedThreads, s, h->nu, mt, sargs(h->Enon), ys, xb, z, r,
+    pdl_launch(k_combine<XT>, kRedBlocks, kRedThreads, s, h->nu, mt, sargs(h->Enon), (const float *)h->Enon_vf, ys, xb, z, r,
                                                      h->q, neu, flex, first, 1.0 / (double)h->nu, h->scal,
                                                      h->red + 5 * kRedBlocks * C_Z, h->ctr + C_Z,
                                                      persist ? persist_err(h) : nullptr, h->coef);
