@@ -16,6 +16,8 @@
 
 #include <algorithm>
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace vemg {
@@ -86,6 +88,10 @@ struct BatchWork {
     BChain *bsurf = nullptr, *bbar = nullptr;
     CsrP Aout{};
     const int *caller_of = nullptr;   // caller id of each unknown (internal order)
+    // FP32 V-cycles: E~'s values in FP32 (the prolongation z = E~ y_s is formed in FP32) and an
+    // FP32 copy of the A_bar part of the outer residual (the finest level's right-hand side,
+    // converted once per application instead of on every read)
+    float *Ev32 = nullptr, *Rb32 = nullptr;
     ~BatchWork() {
         delete bsurf;
         delete bbar;
@@ -98,6 +104,11 @@ static double *gsc(BatchWork *w) { return w->sc + B_COUNT * w->K; }
 // batched CSR row operations (natural order)
 
 enum { BOP_SPMV = 0, BOP_SPMV_ADD = 1, BOP_SOR = 2, BOP_RES = 3 };
+
+__global__ void k_bto_float(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
 
 // Rows idx in [0, nrows): row = rows ? rows[idx] : r0 + idx, a group of KW lanes per row, columns
 // c = lane % KW + j KW. SOR skips the diagonal entry and, when sweeping from x = 0 (cur >= 0), every
@@ -560,13 +571,24 @@ static void bprecond(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
                                                            b0, K, nullptr, -1, h->side);
         bvcycle<XT, XT>(*W->bsurf, W, 0, 0, (const XT *)b0, x0, h->side);
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_join, h->side));
-        bvcycle<XT, double>(*W->bbar, W, 1, 0, W->R + (int64_t)mt * K, xb, s);
+        const int64_t nbk = (int64_t)(h->n - mt) * K;
+        if (std::is_same<XT, float>::value && W->Rb32) {
+            k_bto_float<<<grid_for(nbk, 256), 256, 0, s>>>(nbk, W->R + (int64_t)mt * K, W->Rb32);
+            BATCH_LAUNCHED();
+            bvcycle<XT, XT>(*W->bbar, W, 1, 0, (const XT *)W->Rb32, xb, s);
+        } else {
+            bvcycle<XT, double>(*W->bbar, W, 1, 0, W->R + (int64_t)mt * K, xb, s);
+        }
         VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
-        // z = E~ y_s + [0; x_bar]
-        bcsr<BOP_SPMV, double, XT, double, double, double>(CsrP{h->E.rp, h->E.ci, h->E.v}, h->n, nullptr, 0,
-                                                           (const double *)nullptr, (const double *)nullptr, x0, W->Z,
-                                                           K, nullptr, -1, s);
-        int64_t nbk = (int64_t)(h->n - mt) * K;
+        // z = E~ y_s + [0; x_bar] (in FP32 with FP32 V-cycles, converted once into the FP64 z)
+        if (std::is_same<XT, float>::value && W->Ev32)
+            bcsr<BOP_SPMV, float, XT, double, double, float>(CsrP{h->E.rp, h->E.ci, W->Ev32}, h->n, nullptr, 0,
+                                                            (const float *)nullptr, (const double *)nullptr, x0,
+                                                            W->Z, K, nullptr, -1, s);
+        else
+            bcsr<BOP_SPMV, double, XT, double, double, double>(CsrP{h->E.rp, h->E.ci, h->E.v}, h->n, nullptr, 0,
+                                                               (const double *)nullptr, (const double *)nullptr, x0,
+                                                               W->Z, K, nullptr, -1, s);
         k_badd<XT><<<grid_for(nbk, 256), 256, 0, s>>>(nbk, xb, W->Z + (int64_t)mt * K);
         BATCH_LAUNCHED();
     } else {
@@ -850,6 +872,12 @@ BatchWork *new_batch_work(vemg_hierarchy *h, int K, cudaStream_t s) {
             W->lb[ch][l] = ar.alloc<char>((int64_t)es * m);
             W->lr[ch][l] = ar.alloc<char>((int64_t)es * m);
         }
+    if (fp32 && !single_chain(h)) {
+        W->Ev32 = ar.alloc<float>(h->E.nnz);
+        k_bto_float<<<grid_for(h->E.nnz, 256), 256, 0, s>>>(h->E.nnz, (const double *)h->E.v, W->Ev32);
+        VEMG_CHECK_LAUNCH();
+        W->Rb32 = ar.alloc<float>((int64_t)(h->n - h->mtop) * K);
+    }
     W->sc = ar.alloc<double>(B_COUNT * K + G_COUNT);
     W->part = ar.alloc<double>((int64_t)5 * stage1_blocks(N) * K);
     W->ctr = ar.alloc<unsigned>(2);
