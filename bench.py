@@ -35,6 +35,7 @@ METRIC = "solves/s at FP64 rel-res 1e-8"
 
 
 PRECONDS = {"additive": 0, "vl_sor": 1, "sa": 2}
+SOR_FINE_DRAM_RATIO = 21.2 / 20.2   # ncu DRAM bytes / algorithmic bytes, finest FP32 colour sweep
 CYCLES = {"persistent": 0, "launches": 1, "auto": 2}
 
 
@@ -539,9 +540,16 @@ def main():
     if classes:
         dom = max((c for c in classes if c != "sor_all"), key=lambda c: classes[c]["ms_per_solve"])
         c = classes[dom]
+        # DRAM traffic per launch of the finest-level FP32 colour sweep, from one ncu capture on a
+        # 192x192x32 mesh: 1.05 x its algorithmic bytes, scaled here by this workload's bytes per launch
+        traffic = None
+        if dom == "sor_fine" and args.precision == "fp32":
+            traffic = {"bytes_per_launch": SOR_FINE_DRAM_RATIO * c["bytes_per_launch"],
+                       "source": "ncu dram__bytes (read + write) of one k_sell_sor<float, float, double> launch on a "
+                                 "192x192x32 mesh, scaled by algorithmic bytes per launch"}
         roofline = {"bound": "hbm", "kernel": dom, "achieved": c["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                     "frac": c["achieved_gbs"] / hbm, "peak_source": f"{peak_kind} hbm_gbs (copy, burst)",
-                    "traffic": None, "classes": classes}
+                    "traffic": traffic, "classes": classes}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
