@@ -8,7 +8,7 @@ relative residual 1e-8. A step is one complete solve (every Krylov iteration wit
 multigrid preconditioner) with the hierarchy resident on the device; the hierarchy is built once
 (its time is reported as setup_s). Inputs (A: 0.39 GB, hierarchy > 1 GB) are larger than L2.
 
-  python bench.py [--steps K] [--warmup W] [--precision fp64|fp32] [--impl vemg|reference]
+  python bench.py [--steps K] [--warmup W] [--precision fp64|fp32|bf16] [--impl vemg|reference]
 
 Under torchrun (N > 1), every rank solves its own right-hand sides on its own GPU (independent
 problems, no collective in the data path); value = solves of all ranks / max rank time.
@@ -35,6 +35,9 @@ METRIC = "solves/s at FP64 rel-res 1e-8"
 
 
 PRECONDS = {"additive": 0, "vl_sor": 1, "sa": 2}
+PRECS = {"fp64": 0, "fp32": 1, "bf16": 2}
+DTYPES = {"fp64": "f64", "fp32": "f64 outer + f32 preconditioner",
+          "bf16": "f64 outer + f32 preconditioner with bf16 operator values"}
 SOR_FINE_DRAM_RATIO = 21.2 / 20.2   # ncu DRAM bytes / algorithmic bytes, finest FP32 colour sweep
 CYCLES = {"persistent": 0, "launches": 1, "auto": 2}
 
@@ -45,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vemg", choices=["vemg", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp32", choices=list(PRECS))
     ap.add_argument("--cycle", default="auto", choices=["auto", "persistent", "launches"],
                     help="one cooperative kernel per preconditioner application, one kernel per phase, or the "
                          "library's choice by precision")
@@ -337,7 +340,7 @@ def run_serve(args):
     import torch
     from paper_0912_1976_gb300 import serve as S
     from paper_0912_1976_gb300 import vemg as V
-    prec = V.VEMG_PREC_FP64 if args.precision == "fp64" else V.VEMG_PREC_FP32
+    prec = PRECS[args.precision]
     fac = S.GpuFactory(slots=8, precision=prec)
     for i in range(len(S.SIZES)):                  # meshes are inputs: generated before the clock
         fac.mesh(i, 1.0)
@@ -361,7 +364,7 @@ def run_serve(args):
             "unit": "solves/s", "n_gpus": 1, "steps": args.serve, "warmup": 0,
             "ms_per_step": 1000.0 * p["makespan_s"] / max(p["requests"], 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f64 outer + f32 preconditioner", "data": "synthetic",
+            "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": f"serve{args.serve}: Poisson arrivals at {rate:.2f}/s over 8 meshes "
                                    "(44..399 squared x 24 layers, z-jitter 0.3), eps in {1e-4,1e-3,1e-2,1e-1}, "
                                    "Neumann/Dirichlet-top 50/50, 1-8 RHS per request, 8-slot engines, rtol 1e-8",
@@ -412,7 +415,7 @@ def run_case(args):
     m = I.make_mesh(nx, ny, nz, I.depth_sines(1e-3), z_jitter=0.3, seed=77)
     vm = V.Mesh.from_inputs(m)
     A = V.vemg_assemble(vm)
-    prec = V.VEMG_PREC_FP64 if args.precision == "fp64" else V.VEMG_PREC_FP32
+    prec = PRECS[args.precision]
     h = V.vemg_setup(A, vm, V.vemg_default_options(precision=prec, precond=PRECONDS[args.precond],
                                                    cycle=CYCLES[args.cycle]))
     if args.phases:
@@ -518,12 +521,12 @@ def main():
         t0 = time.perf_counter()
         A = V.vemg_assemble(vm)
         h = V.vemg_setup(A, vm, V.vemg_default_options(
-            precision=V.VEMG_PREC_FP64 if prec == "fp64" else V.VEMG_PREC_FP32, precond=PRECONDS[args.precond],
+            precision=PRECS[prec], precond=PRECONDS[args.precond],
             cycle=CYCLES[args.cycle]))
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         # VEMG_CYCLE_AUTO resolves to the persistent kernel for FP64 V-cycles
-        persistent = args.cycle == "persistent" or (args.cycle == "auto" and prec == "fp64")
+        persistent = prec != "bf16" and (args.cycle == "persistent" or (args.cycle == "auto" and prec == "fp64"))
         r = measure(args, h, B, n, ws, rank, local, dist, V, torch, probe=not args.no_probe, persistent=persistent)
         r["cycle"] = "persistent" if persistent else "launches"
         r["setup_s"] = setup_s
@@ -570,7 +573,7 @@ def main():
         line = {"metric": METRIC, "value": head["value"], "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if args.precision == "fp64" else "f64 outer + f32 preconditioner",
+                "dtype": DTYPES[args.precision],
                 "data": "synthetic", "config": workload_config(args, n),
                 "gdof_iter_per_s": head["gdof_iter_per_s"], "iters": head["iters"],
                 "true_relres_max": head["true_relres_max"], "setup_s": head["setup_s"],

@@ -70,6 +70,11 @@ extern "C" {
 /* precision of the preconditioner; the outer Krylov loop is always FP64 */
 #define VEMG_PREC_FP64 0   /* everything FP64, CG outer loop */
 #define VEMG_PREC_FP32 1   /* V-cycle values, vectors and arithmetic FP32, flexible CG outer loop */
+#define VEMG_PREC_BF16 2   /* as FP32, with the off-diagonal values of the V-cycle operators (A, P,
+                              P^T of every level) rounded to BF16 (from FP32, nearest even) and
+                              stored in BF16; diagonals, vectors and sums FP32. The cycle runs one
+                              kernel per phase; the batched solves and the single-CTA coarse tail
+                              read FP32 copies of the same rounded values */
 
 /* Tetrahedral mesh, HOST pointers (section 2.1, section 3).
    xyz: n_nodes x 3 doubles (x, y, z), z up, top surface at the largest z of each column.
@@ -98,7 +103,7 @@ typedef struct vemg_csr {
 
 typedef struct vemg_options {
     int bc;           /* VEMG_NEUMANN or VEMG_DIRICHLET_TOP */
-    int precision;    /* VEMG_PREC_FP64 or VEMG_PREC_FP32 */
+    int precision;    /* VEMG_PREC_FP64, VEMG_PREC_FP32 or VEMG_PREC_BF16 */
     double strength;  /* SA strong-coupling threshold, section 6: 0.01 */
     double omega_p;   /* SA prolongator smoothing weight, section 6: 2/3 */
     int coarse_max;   /* a level of at most this many rows is solved directly (dense) */

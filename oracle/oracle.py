@@ -63,9 +63,13 @@ def lib():
         L.or_vcycle.argtypes = [C.c_void_p, C.c_int, dp, dp]
         L.or_sa_aggregate.argtypes = [C.c_int, ip, ip, dp, C.c_double, ip]
         L.or_colour.argtypes = [C.c_int, ip, ip, ip]
+        L.or_sl_ranks.argtypes = [C.c_int, ip, ip, ip]
         L.or_locate_points.argtypes = [C.c_int, ip, dp, C.c_int, dp, ip, dp]
         L.or_elem_stiffness.restype = C.c_double
         L.or_elem_stiffness.argtypes = [dp, dp]
+        L.or_round_bf16.argtypes = [C.c_double]
+        L.or_round_bf16.restype = C.c_double
+        L.or_round_operators_bf16.argtypes = [C.c_void_p]
         _lib = L
     return _lib
 
@@ -191,6 +195,16 @@ class Problem:
         lib().or_vcycle(self.h, which, _p(b, C.c_double), _p(x, C.c_double))
         return x
 
+    def round_operators_bf16(self):
+        """Round the stored cycle operators to BF16 (off-diagonals of every level matrix, P and
+        P^T), in place: the operator the BF16 variant of the cycle applies."""
+        lib().or_round_operators_bf16(self.h)
+
+
+def round_bf16(a: float) -> float:
+    """a rounded to binary32, then to bfloat16 (nearest, ties to even)."""
+    return lib().or_round_bf16(float(a))
+
 
 def sa_aggregate(A: sp.csr_matrix, theta=THETA):
     A = A.tocsr()
@@ -209,6 +223,16 @@ def colour(A: sp.csr_matrix):
     col = np.zeros(A.shape[0], np.int32)
     nc = lib().or_colour(A.shape[0], _p(rp, C.c_int), _p(ci, C.c_int), _p(col, C.c_int))
     return nc, col
+
+
+def sl_ranks(A: sp.csr_matrix):
+    """Round of removal of each node in the round-synchronous smallest-last peeling."""
+    A = A.tocsr()
+    A.sort_indices()
+    rp, ci = _i32(A.indptr), _i32(A.indices)
+    rank = np.zeros(A.shape[0], np.int32)
+    lib().or_sl_ranks(A.shape[0], _p(rp, C.c_int), _p(ci, C.c_int), _p(rank, C.c_int))
+    return rank
 
 
 def locate_points(tris, xyz, pts_xy):

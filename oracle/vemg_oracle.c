@@ -28,8 +28,9 @@
  *     residual (section 3, the BoLe05 remark), or flexible CG (Notay's FCG(1)).
  *
  * Readings where the paper is silent (all shared with the GPU path by definition, not by code):
- *   aggregation and SOR ordering are made round-synchronous (distance-2 maximal independent
- *   sets and Jones-Plassmann colouring with a fixed integer hash), the Galerkin product is
+ *   aggregation is made round-synchronous (distance-2 maximal independent sets with a fixed
+ *   integer hash), the SOR ordering is multicolour with the colours of a greedy colouring in
+ *   round-synchronous smallest-last order (ties broken by the same hash), the Galerkin product is
  *   P^T (A P) with entries summed in ascending index order and the lower triangle copied from
  *   the upper, the coarsest level is a dense Cholesky solve (regularised by a rank-one term
  *   on the singular surface chain).
@@ -273,7 +274,7 @@ typedef struct {
     csr P, PT;    /* transfer to the next coarser level (absent on the coarsest) */
     int *agg;     /* aggregate of each node (absent on the coarsest) */
     int ncolours;
-    int *colour;  /* Jones-Plassmann colour of each node */
+    int *colour;  /* SOR colour of each node (smallest-last greedy) */
     int *cptr;    /* ncolours + 1 offsets into crow */
     int *crow;    /* rows grouped by colour, ascending within a colour */
     double *x, *b, *r; /* work vectors */
@@ -427,44 +428,89 @@ int or_sa_aggregate(int n, const int *rp, const int *ci, const double *v, double
     return nagg;
 }
 
-/* Jones-Plassmann colouring on the matrix graph: in each round every uncoloured node whose
-   key (hash32(i), i) exceeds the keys of all its uncoloured neighbours takes the smallest
-   colour not used by an already-coloured neighbour. Returns the number of colours. */
+/* Round-synchronous smallest-last ranks (a k-core peeling): round t first sets the threshold
+   k_t = max(k_{t-1}, the smallest remaining degree), k_{-1} = 0, then removes every remaining
+   node with at most k_t remaining neighbours and gives it the rank t. Every round removes at
+   least one node. The nodes that qualify in the next round at the same threshold are
+   neighbours of the removed ones, so a round costs the work of the nodes it removes; only
+   a raise of the threshold scans all remaining nodes. */
+void or_sl_ranks(int n, const int *rp, const int *ci, int *rank) {
+    int *deg = (int *)xcalloc((size_t)n, sizeof(int));
+    int *cur = (int *)xcalloc((size_t)n, sizeof(int));
+    int *nxt = (int *)xcalloc((size_t)n, sizeof(int));
+    char *queued = (char *)xcalloc((size_t)n, 1);
+    for (int i = 0; i < n; ++i) {
+        for (int k = rp[i]; k < rp[i + 1]; ++k) if (ci[k] != i) deg[i]++;
+        rank[i] = -1;
+    }
+    int left = n, k = 0, ncur = 0;
+    for (int round = 0; left > 0; ++round) {
+        if (ncur == 0) {
+            /* nothing at or below the threshold: raise it to the smallest remaining degree */
+            int dmin = -1;
+            for (int i = 0; i < n; ++i)
+                if (rank[i] < 0 && (dmin < 0 || deg[i] < dmin)) dmin = deg[i];
+            if (dmin > k) k = dmin;
+            for (int i = 0; i < n; ++i)
+                if (rank[i] < 0 && deg[i] <= k) { cur[ncur++] = i; queued[i] = 1; }
+        }
+        for (int t = 0; t < ncur; ++t) rank[cur[t]] = round;
+        left -= ncur;
+        int nn = 0;
+        for (int t = 0; t < ncur; ++t) {
+            int i = cur[t];
+            for (int q = rp[i]; q < rp[i + 1]; ++q) {
+                int j = ci[q];
+                if (j == i || rank[j] >= 0) continue;
+                deg[j]--;
+                if (deg[j] <= k && !queued[j]) { queued[j] = 1; nxt[nn++] = j; }
+            }
+        }
+        int *sw = cur; cur = nxt; nxt = sw;
+        ncur = nn;
+    }
+    free(deg); free(cur); free(nxt); free(queued);
+}
+
+static const int *g_key_rank;   /* comparator context of the colouring order */
+static int cmp_key_desc(const void *a, const void *b) {
+    int i = *(const int *)a, j = *(const int *)b;
+    uint64_t ki = ((uint64_t)(uint32_t)g_key_rank[i] << 32) | hash32((uint32_t)i);
+    uint64_t kj = ((uint64_t)(uint32_t)g_key_rank[j] << 32) | hash32((uint32_t)j);
+    return ki < kj ? 1 : (ki > kj ? -1 : 0);
+}
+
+/* Colouring of the matrix graph for the multicolour SOR sweeps: greedy first-fit in
+   smallest-last order. Nodes are coloured by decreasing key (rank, hash32(i)) -- removed last,
+   coloured first, ties in a round broken by the fixed hash -- each taking the smallest colour
+   that no already coloured neighbour has. A node's already coloured neighbours were all still
+   present when its round began, so it meets at most that round's threshold of them; the
+   threshold never exceeds the graph's degeneracy (it only rises to a minimum degree of a
+   subgraph), so the colours number at most the degeneracy + 1. Returns the number of colours. */
 int or_colour(int n, const int *rp, const int *ci, int *colour) {
-    uint64_t *key = (uint64_t *)xcalloc((size_t)n, sizeof(uint64_t));
-    for (int i = 0; i < n; ++i) key[i] = ((uint64_t)hash32((uint32_t)i) << 32) | (uint64_t)(uint32_t)i;
-    for (int i = 0; i < n; ++i) colour[i] = -1;
-    char *win = (char *)xcalloc((size_t)n, 1);
+    int *rank = (int *)xcalloc((size_t)n, sizeof(int));
+    int *order = (int *)xcalloc((size_t)n, sizeof(int));
+    or_sl_ranks(n, rp, ci, rank);
+    for (int i = 0; i < n; ++i) { order[i] = i; colour[i] = -1; }
+    g_key_rank = rank;
+    qsort(order, (size_t)n, sizeof(int), cmp_key_desc);
     int maxdeg = 0;
     for (int i = 0; i < n; ++i) if (rp[i + 1] - rp[i] > maxdeg) maxdeg = rp[i + 1] - rp[i];
     char *used = (char *)xcalloc((size_t)maxdeg + 2, 1);
-    int ncol = 0, left = n;
-    while (left > 0) {
-        for (int i = 0; i < n; ++i) {
-            win[i] = 0;
-            if (colour[i] >= 0) continue;
-            int w = 1;
-            for (int k = rp[i]; k < rp[i + 1] && w; ++k) {
-                int j = ci[k];
-                if (j != i && colour[j] < 0 && key[j] > key[i]) w = 0;
-            }
-            win[i] = (char)w;
+    int ncol = 0;
+    for (int t = 0; t < n; ++t) {
+        int i = order[t];
+        memset(used, 0, (size_t)maxdeg + 2);
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            int j = ci[k];
+            if (j != i && colour[j] >= 0 && colour[j] <= maxdeg) used[colour[j]] = 1;
         }
-        for (int i = 0; i < n; ++i) {
-            if (!win[i]) continue;
-            memset(used, 0, (size_t)maxdeg + 2);
-            for (int k = rp[i]; k < rp[i + 1]; ++k) {
-                int j = ci[k];
-                if (j != i && colour[j] >= 0 && colour[j] <= maxdeg) used[colour[j]] = 1;
-            }
-            int c = 0;
-            while (used[c]) c++;
-            colour[i] = c;
-            if (c + 1 > ncol) ncol = c + 1;
-            left--;
-        }
+        int c = 0;
+        while (used[c]) c++;
+        colour[i] = c;
+        if (c + 1 > ncol) ncol = c + 1;
     }
-    free(key); free(win); free(used);
+    free(rank); free(order); free(used);
     return ncol;
 }
 
@@ -1248,6 +1294,49 @@ int or_vcycle(void *hp, int which, const double *b, double *x) {
 }
 
 /* element stiffness of one tetrahedron (for the closed-form test); returns det = 6 V */
+/* ------------------------------------------------------------------------------------------ */
+/* BF16 operator values                                                                        */
+
+/* a rounded to binary32 (the C conversion, nearest even), then to bfloat16, the format with
+   binary32's sign and 8-bit exponent and 7 stored significand bits: keep the upper 16 bits of
+   the binary32 pattern and round the dropped 16 bits to nearest, ties to the even result.
+   Adding one unit of the kept part to the magnitude carries into the exponent where it must
+   (up to infinity). Infinities and NaNs pass through. */
+double or_round_bf16(double a) {
+    float f = (float)a;
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (double)f;
+    uint32_t kept = u & 0xffff0000u, dropped = u & 0x0000ffffu;
+    if (dropped > 0x8000u || (dropped == 0x8000u && (kept & 0x00010000u))) kept += 0x00010000u;
+    memcpy(&f, &kept, sizeof f);
+    return (double)f;
+}
+
+static void round_offdiag_bf16(csr *a, int keep_diagonal) {
+    for (int i = 0; i < a->n; ++i)
+        for (int k = a->rp[i]; k < a->rp[i + 1]; ++k)
+            if (!(keep_diagonal && a->ci[k] == i)) a->v[k] = or_round_bf16(a->v[k]);
+}
+
+/* the operators of every level of every chain, as the BF16 variant of the cycle stores them:
+   off-diagonal entries of each level matrix and every entry of P and P^T rounded to BF16; the
+   diagonal and the dense coarsest factor keep their FP64 values (the setup is unchanged, only
+   the stored operators of the cycle are rounded) */
+void or_round_operators_bf16(void *hp) {
+    problem *h = (problem *)hp;
+    chain *cs[3] = {&h->surf, &h->bar, &h->one};
+    for (int c = 0; c < 3; ++c)
+        for (int l = 0; l < cs[c]->nlev; ++l) {
+            level *L = &cs[c]->lv[l];
+            round_offdiag_bf16(&L->A, 1);
+            if (l + 1 < cs[c]->nlev) {
+                round_offdiag_bf16(&L->P, 0);
+                round_offdiag_bf16(&L->PT, 0);
+            }
+        }
+}
+
 double or_elem_stiffness(const double *p, double *K) {
     return elem_stiffness(p, p + 3, p + 6, p + 9, K);
 }

@@ -618,7 +618,7 @@ static void bstage2(vemg_hierarchy *h, BatchWork *W, int op, int ns, int64_t N, 
 }
 
 static void bprecond_any(vemg_hierarchy *h, BatchWork *W, int first, cudaStream_t s) {
-    if (h->precision == VEMG_PREC_FP32) bprecond<float>(h, W, s);
+    if (h->precision != VEMG_PREC_FP64) bprecond<float>(h, W, s);   // BF16 hierarchies: FP32 values here
     else bprecond<double>(h, W, s);
     // t0 = sum z, t1 = (r, z), t2 = sum r [, t3 = (z, q), t4 = sum q]
     int64_t N = (int64_t)h->nu * W->K;
@@ -852,7 +852,7 @@ BatchWork *new_batch_work(vemg_hierarchy *h, int K, cudaStream_t s) {
     W->B = ar.alloc<double>(N);
     VEMG_CHECK_CUDA(cudaMemsetAsync(W->Q, 0, sizeof(double) * N, s));
     VEMG_CHECK_CUDA(cudaMemsetAsync(W->Z, 0, sizeof(double) * N, s));
-    const bool fp32 = h->precision == VEMG_PREC_FP32;
+    const bool fp32 = h->precision != VEMG_PREC_FP64;
     size_t es = fp32 ? sizeof(float) : sizeof(double);
     const Chain *chains[2] = {&h->surf, single_chain(h) ? &the_chain(h) : &h->bar};
     if (!single_chain(h)) W->bsurf = build_bchain(h->surf, fp32, ar, s);

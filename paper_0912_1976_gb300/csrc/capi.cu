@@ -253,7 +253,8 @@ int vemg_setup(const vemg_csr *A, const vemg_mesh *mesh, const vemg_options *opt
         vemg_default_options(&o);
         if (opts) o = *opts;
         if ((o.bc != VEMG_NEUMANN && o.bc != VEMG_DIRICHLET_TOP) ||
-            (o.precision != VEMG_PREC_FP64 && o.precision != VEMG_PREC_FP32) || !(o.strength >= 0.0) ||
+            (o.precision != VEMG_PREC_FP64 && o.precision != VEMG_PREC_FP32 && o.precision != VEMG_PREC_BF16) ||
+            !(o.strength >= 0.0) ||
             !(o.omega_p > 0.0) || o.coarse_max < 1 || o.coarse_max > 1024 || o.max_levels < 1 ||
             o.max_levels > kMaxLevels || o.precond < VEMG_PRECOND_ADDITIVE || o.precond > VEMG_PRECOND_NONE ||
             (o.precond == VEMG_PRECOND_VL_SOR && o.bc != VEMG_NEUMANN) ||
@@ -264,6 +265,7 @@ int vemg_setup(const vemg_csr *A, const vemg_mesh *mesh, const vemg_options *opt
             o.precision = VEMG_PREC_FP64;
             o.cycle = VEMG_CYCLE_LAUNCHES;
         }
+        if (o.precision == VEMG_PREC_BF16) o.cycle = VEMG_CYCLE_LAUNCHES;   // BF16 values: per-phase kernels
         if (o.cycle == VEMG_CYCLE_AUTO)
             o.cycle = o.precision == VEMG_PREC_FP64 ? VEMG_CYCLE_PERSISTENT : VEMG_CYCLE_LAUNCHES;
         h->opts = o;

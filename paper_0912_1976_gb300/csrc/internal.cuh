@@ -164,6 +164,7 @@ struct Sell {
     bool fp32 = false;
     int64_t nnz = 0;          // stored (unpadded) entries
     int64_t padded = 0;       // stored entries including padding
+    void *vh = nullptr;       // BF16 copy of the FP32 values (BF16 precision), else null
 };
 
 // One multigrid level in solve order: rows grouped by colour (colour-major, ascending natural

@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <cstring>
 
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 namespace vemg {
@@ -167,7 +169,29 @@ __global__ void k_permute_dense(int n, const int *__restrict__ s2n, const double
     Gs[t] = G[(int64_t)s2n[a] * n + s2n[b]];
 }
 
-static void layout_chain(Arena &ar, const Chain &C, SChain &S, bool fp32, cudaStream_t s) {
+// b = a rounded to BF16 (nearest, ties to even); a is overwritten by the same value in FP32
+__global__ void k_f2bf(int64_t n, float *__restrict__ a, __nv_bfloat16 *__restrict__ b) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        __nv_bfloat16 h = __float2bfloat16_rn(a[i]);
+        b[i] = h;
+        a[i] = __bfloat162float(h);
+    }
+}
+
+// BF16 values of a sliced-ELL matrix, rounded from its FP32 values. The FP32 array keeps the
+// rounded values, so that the kernels that read it (the batched solves, the coarse tails, the
+// persistent cycle) apply the same operator as the per-phase kernels that read the BF16 array.
+static void to_bf16(Arena &ar, Sell &S, cudaStream_t s) {
+    __nv_bfloat16 *v = ar.alloc<__nv_bfloat16>(S.padded > 0 ? S.padded : 1);
+    if (S.padded > 0) {
+        k_f2bf<<<grid_for(S.padded, 256), 256, 0, s>>>(S.padded, (float *)S.v, v);
+        VEMG_CHECK_LAUNCH();
+    }
+    S.vh = v;
+}
+
+static void layout_chain(Arena &ar, const Chain &C, SChain &S, bool fp32, cudaStream_t s, bool bf16 = false) {
     S.nlev = C.nlev;
     S.direct = C.direct;
     S.singular = C.singular;
@@ -195,6 +219,13 @@ static void layout_chain(Arena &ar, const Chain &C, SChain &S, bool fp32, cudaSt
                              nullptr, s);
             T.PT = build_sell(ar, L.PT, N.A.n, N.crow, inv[l], L.A.n, {0, N.A.n}, false, fp32, nullptr, nullptr,
                               nullptr, s);
+        }
+        if (bf16) {
+            to_bf16(ar, T.A, s);
+            if (l + 1 < C.nlev) {
+                to_bf16(ar, T.P, s);
+                to_bf16(ar, T.PT, s);
+            }
         }
         size_t es = fp32 ? sizeof(float) : sizeof(double);
         T.x = ar.alloc<char>((int64_t)es * T.n);
@@ -234,11 +265,12 @@ __global__ void k_iota(int n, int *out) {
 
 void build_solve_layout(vemg_hierarchy *h, cudaStream_t s) {
     Arena &ar = h->arena;
-    bool fp32 = h->precision == VEMG_PREC_FP32;
+    bool fp32 = h->precision != VEMG_PREC_FP64;
+    bool bf16 = h->precision == VEMG_PREC_BF16;
     int n = h->n, mt = h->mtop;
     if (!single_chain(h)) {
-        layout_chain(ar, h->bar, h->sbar, fp32, s);
-        layout_chain(ar, h->surf, h->ssurf, fp32, s);
+        layout_chain(ar, h->bar, h->sbar, fp32, s, bf16);
+        layout_chain(ar, h->surf, h->ssurf, fp32, s, bf16);
         h->nu = n;
         Scratch<int> s2n(n), n2s(n);
         k_outer_order<<<grid_for(n, 256), 256, 0, s>>>(n, mt, h->surf.lv[0].crow, h->bar.lv[0].crow, s2n);
@@ -276,7 +308,7 @@ void build_solve_layout(vemg_hierarchy *h, cudaStream_t s) {
         // one chain whose level 0 is the operator of the unknowns (A_bar for Dirichlet-top, A for
         // the VL_SOR / SA preconditioners); the outer vectors use its level-0 colour order
         const Chain &C = the_chain(h);
-        layout_chain(ar, C, h->sbar, fp32, s);
+        layout_chain(ar, C, h->sbar, fp32, s, bf16);
         int off = h->bc == VEMG_DIRICHLET_TOP ? mt : 0;
         int nb = n - off;
         h->nu = nb;

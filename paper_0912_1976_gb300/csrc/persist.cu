@@ -511,7 +511,7 @@ static int max_blocks_per_sm() {
 
 void build_persist(vemg_hierarchy *h, cudaStream_t s) {
     if (h->persist) return;
-    const bool fp32 = h->precision == VEMG_PREC_FP32;
+    const bool fp32 = h->precision != VEMG_PREC_FP64;
     const bool two = !single_chain(h);
     Builder B(h->arena, s);
     B.xs = fp32 ? 4 : 8;
@@ -606,7 +606,7 @@ static void build_tail(Arena &ar, SChain &C, bool fp32, cudaStream_t s) {
 }
 
 void build_tails(vemg_hierarchy *h, cudaStream_t s) {
-    const bool fp32 = h->precision == VEMG_PREC_FP32;
+    const bool fp32 = h->precision != VEMG_PREC_FP64;
     if (h->precond == VEMG_PRECOND_NONE) return;
     if (!single_chain(h)) build_tail(h->arena, h->ssurf, fp32, s);
     build_tail(h->arena, h->sbar, fp32, s);

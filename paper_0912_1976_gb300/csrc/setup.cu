@@ -1091,22 +1091,79 @@ __global__ void k_prolong_fill(int n, const int *__restrict__ rp, const int *__r
 }
 
 // ------------------------------------------------------------------------------------------
-// Jones-Plassmann colouring
+// SOR colouring: greedy first-fit in round-synchronous smallest-last order
+//
+// Peeling: round t sets the threshold k_t = max(k_{t-1}, smallest remaining degree), k_{-1} = 0,
+// and removes every remaining node with at most k_t remaining neighbours, giving it the rank t
+// (a k-core peeling; every round removes at least one node). Colouring: a node takes
+// the smallest colour absent from its coloured neighbours once every neighbour of larger key
+// (rank, hash32(i)) is coloured (Jones-Plassmann rounds). With fixed distinct keys, Jones-
+// Plassmann gives exactly the greedy colouring in decreasing key order: when a node is coloured,
+// its coloured neighbours are precisely those of larger key.
 
-__global__ void k_jp_winners(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                             const int *__restrict__ colour, int *win, int *left) {
+static constexpr int kRoundBatch = 32;   // rounds launched between two host checks
+
+__device__ __forceinline__ uint64_t colour_key(int rank, int i) {
+    return ((uint64_t)(uint32_t)rank << 32) | hash32((uint32_t)i);
+}
+
+__global__ void k_offdiag_degree(int n, const int *__restrict__ rp, const int *__restrict__ ci, int *deg,
+                                 int *rank) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    int d = 0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) d += ci[k] != i;
+    deg[i] = d;
+    rank[i] = -1;
+}
+
+// the minimum remaining degree (dmin) and the number of remaining nodes (alive) of one round
+__global__ void k_sl_min(int n, const int *__restrict__ deg, const int *__restrict__ rank, int *dmin, int *alive) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool in = i < n && rank[i] < 0;
+    unsigned d = in ? (unsigned)deg[i] : 0xffffffffu;
+    unsigned m = __reduce_min_sync(0xffffffffu, d);
+    unsigned c = __popc(__ballot_sync(0xffffffffu, in));
+    if ((threadIdx.x & 31) == 0 && c > 0) {
+        atomicMin(dmin, (int)m);
+        atomicAdd(alive, (int)c);
+    }
+}
+
+// kth[0] holds the previous round's threshold; the round's own goes to kth[1]
+__global__ void k_sl_take(int n, const int *__restrict__ deg, int *rank, const int *__restrict__ dmin, int *kth,
+                          int round) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int k = max(kth[0], *dmin);
+    if (i == 0) kth[1] = k;
+    if (i < n && rank[i] < 0 && deg[i] <= k) rank[i] = round;
+}
+
+__global__ void k_sl_update(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                            const int *__restrict__ rank, int *deg, int round) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || rank[i] != round) return;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        int j = ci[k];
+        if (j != i && rank[j] < 0) atomicSub(deg + j, 1);
+    }
+}
+
+__global__ void k_jp_winners(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const int *__restrict__ rank, const int *__restrict__ colour, int *win, int *left) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool unc = i < n && colour[i] < 0;
+    unsigned c = __popc(__ballot_sync(0xffffffffu, unc));
+    if ((threadIdx.x & 31) == 0 && c > 0) atomicAdd(left, (int)c);
+    if (i >= n) return;
     int w = 0;
-    if (colour[i] < 0) {
-        atomicAdd(left, 1);
-        uint64_t ki = ((uint64_t)hash32((uint32_t)i) << 32) | (uint32_t)i;
+    if (unc) {
+        uint64_t ki = colour_key(rank[i], i);
         w = 1;
         for (int k = rp[i]; k < rp[i + 1] && w; ++k) {
             int j = ci[k];
             if (j == i || colour[j] >= 0) continue;
-            uint64_t kj = ((uint64_t)hash32((uint32_t)j) << 32) | (uint32_t)j;
-            if (kj > ki) w = 0;
+            if (colour_key(rank[j], j) > ki) w = 0;
         }
     }
     win[i] = w;
@@ -1145,15 +1202,37 @@ static void colour_level(Arena &ar, Level &L, cudaStream_t s) {
     int n = L.A.n;
     L.colour = ar.alloc<int>(n);
     VEMG_CHECK_CUDA(cudaMemsetAsync(L.colour, 0xff, sizeof(int) * n, s));
-    Scratch<int> win(n), left(1), maxc(1);
+    // per-round slots: every round removes at least one node, so there are at most n rounds
+    // (plus the rounds of the last batch launched after the peeling ended, which do nothing)
+    const int64_t slots = (int64_t)n + kRoundBatch + 2;
+    Scratch<int> deg(n), rank(n), win(n), maxc(1), dmin(slots), kth(slots), cnt(slots);
+    if (n > 0) {
+        k_offdiag_degree<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, deg, rank);
+        VEMG_CHECK_LAUNCH();
+        VEMG_CHECK_CUDA(cudaMemsetAsync(dmin, 0x7f, sizeof(int) * slots, s));   // 0x7f7f7f7f: no node
+        VEMG_CHECK_CUDA(cudaMemsetAsync(kth, 0, sizeof(int) * slots, s));
+        VEMG_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * slots, s));
+    }
+    // peeling, kRoundBatch rounds per host check
+    for (int r0 = 0; n > 0; r0 += kRoundBatch) {
+        for (int t = r0; t < r0 + kRoundBatch; ++t) {
+            k_sl_min<<<grid_for(n, 256), 256, 0, s>>>(n, deg, rank, dmin + t, cnt + t);
+            k_sl_take<<<grid_for(n, 256), 256, 0, s>>>(n, deg, rank, dmin + t, kth + t, t);
+            k_sl_update<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, rank, deg, t);
+            VEMG_CHECK_LAUNCH();
+        }
+        // nodes present at the start of the batch's last round: none means the peeling is done
+        if (read_int(cnt + (r0 + kRoundBatch - 1), s) == 0) break;
+    }
     VEMG_CHECK_CUDA(cudaMemsetAsync(maxc, 0, sizeof(int), s));
-    for (;;) {
-        VEMG_CHECK_CUDA(cudaMemsetAsync(left, 0, sizeof(int), s));
-        k_jp_winners<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, L.colour, win, left);
-        VEMG_CHECK_LAUNCH();
-        k_jp_assign<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, win, L.colour, maxc);
-        VEMG_CHECK_LAUNCH();
-        if (read_int(left, s) == 0) break;
+    for (int batch = 0; n > 0; ++batch) {
+        VEMG_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * kRoundBatch, s));
+        for (int t = 0; t < kRoundBatch; ++t) {
+            k_jp_winners<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, rank, L.colour, win, cnt + t);
+            k_jp_assign<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, win, L.colour, maxc);
+            VEMG_CHECK_LAUNCH();
+        }
+        if (read_int(cnt + (kRoundBatch - 1), s) == 0) break;
     }
     L.ncolours = n > 0 ? read_int(maxc, s) + 1 : 0;
     L.crow = ar.alloc<int>(n);

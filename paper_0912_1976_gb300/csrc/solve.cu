@@ -19,6 +19,8 @@
 
 #include <type_traits>
 
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 namespace vemg {
@@ -109,6 +111,11 @@ static double sell_bytes(int64_t nnz, double vb, int64_t rows, double per_row) {
 // entries instead of two per entry. lim >= 0 skips columns >= lim.
 static constexpr int kU = 16;
 
+// BF16 values widen to FP32 before they meet the vector; FP32 and FP64 values pass through
+__device__ __forceinline__ float float_or_self(__nv_bfloat16 a) { return __bfloat162float(a); }
+__device__ __forceinline__ float float_or_self(float a) { return a; }
+__device__ __forceinline__ double float_or_self(double a) { return a; }
+
 template <class VT, class XT, class AT>
 __device__ __forceinline__ AT sell_row(const int *__restrict__ col, const VT *__restrict__ v, int o, int w,
                                        const XT *x, int lim) {
@@ -120,11 +127,11 @@ __device__ __forceinline__ AT sell_row(const int *__restrict__ col, const VT *__
         for (int u = 0; u < kU; ++u) {
             int k = k0 + u;
             c[u] = k < w ? __ldg(col + o + 32 * k) : 0;
-            a[u] = k < w ? __ldg(v + o + 32 * k) : (VT)0;
+            a[u] = k < w ? __ldg(v + o + 32 * k) : VT{};
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u)
-            if (k0 + u < w && (lim < 0 || c[u] < lim)) acc += (AT)a[u] * (AT)x[c[u]];
+            if (k0 + u < w && (lim < 0 || c[u] < lim)) acc += (AT)(float_or_self(a[u])) * (AT)x[c[u]];
     }
     return acc;
 }
@@ -152,7 +159,7 @@ template <class VT, class XT, class BT>
 __global__ void __launch_bounds__(kSellBlock) k_sell_sor(int s0, int s1, const int *__restrict__ row0,
                                                          const int *__restrict__ nrow, const int *__restrict__ off,
                                                          const int *__restrict__ width, const int *__restrict__ col,
-                                                         const VT *__restrict__ v, const VT *__restrict__ dinv,
+                                                         const VT *__restrict__ v, const XT *__restrict__ dinv,
                                                          const BT *__restrict__ b, XT *x, int lim) {
     pdl_begin();
     int s = s0 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
@@ -168,7 +175,7 @@ template <class VT, class XT, class BT>
 __global__ void __launch_bounds__(kSellBlock) k_sell_residual(int nsl, const int *__restrict__ row0,
                                                               const int *__restrict__ nrow, const int *__restrict__ off,
                                                               const int *__restrict__ width, const int *__restrict__ col,
-                                                              const VT *__restrict__ v, const VT *__restrict__ diag,
+                                                              const VT *__restrict__ v, const XT *__restrict__ diag,
                                                               const BT *__restrict__ b, const XT *__restrict__ x,
                                                               XT *__restrict__ r) {
     pdl_begin();
@@ -200,9 +207,19 @@ template <class VT, class XT, class YT, class AT>
 static void sell_spmv(const Sell &S, const XT *x, YT *y, int add, cudaStream_t s) {
     if (S.nslices == 0) return;
     int64_t threads = (int64_t)S.nslices * 32;
-    pdl_launch(k_sell_spmv<VT, XT, YT, AT>, grid_for(threads, kSellBlock), kSellBlock, s, 
-        0, S.nslices, S.row0, S.nrow, S.off, S.width, S.col, (const VT *)S.v, x, y, add);
+    if (S.vh)   // BF16 values (FP32 vectors)
+        pdl_launch(k_sell_spmv<__nv_bfloat16, XT, YT, AT>, grid_for(threads, kSellBlock), kSellBlock, s, 0,
+                   S.nslices, S.row0, S.nrow, S.off, S.width, S.col, (const __nv_bfloat16 *)S.vh, x, y, add);
+    else
+        pdl_launch(k_sell_spmv<VT, XT, YT, AT>, grid_for(threads, kSellBlock), kSellBlock, s, 0, S.nslices,
+                   S.row0, S.nrow, S.off, S.width, S.col, (const VT *)S.v, x, y, add);
     SOLVE_LAUNCHED();
+}
+
+// bytes of one stored value of S as the per-phase kernels read it
+template <class XT>
+static double value_bytes(const Sell &S) {
+    return S.vh ? 2.0 : (double)sizeof(XT);
 }
 
 template <class XT, class BT>
@@ -215,22 +232,32 @@ static void sor_sweep(const SLevel &L, const BT *b, XT *x, bool forward, bool fr
         int rows = L.crow[c + 1] - L.crow[c];
         // stored entries of the colour (none when lim == 0), b / dinv / x-write per row, and one
         // read of the level's x shared among the sweep's colours
-        double bytes = sell_bytes(lim == 0 ? 0 : L.cnnz[c], sizeof(XT), rows, 3.0 * sizeof(XT)) +
+        double bytes = sell_bytes(lim == 0 ? 0 : L.cnnz[c], value_bytes<XT>(L.A), rows, 3.0 * sizeof(XT)) +
                        (double)sizeof(XT) * L.n / L.ncolours;
         ProbeScope ps(fine ? PROBE_SOR_FINE : PROBE_SOR, bytes, s);
         int64_t threads = (int64_t)(s1 - s0) * 32;
-        pdl_launch(k_sell_sor<XT, XT, BT>, grid_for(threads, kSellBlock), kSellBlock, s, 
-            s0, s1, L.A.row0, L.A.nrow, L.A.off, L.A.width, L.A.col, (const XT *)L.A.v, (const XT *)L.dinv, b, x, lim);
+        if (L.A.vh)
+            pdl_launch(k_sell_sor<__nv_bfloat16, XT, BT>, grid_for(threads, kSellBlock), kSellBlock, s, s0, s1,
+                       L.A.row0, L.A.nrow, L.A.off, L.A.width, L.A.col, (const __nv_bfloat16 *)L.A.vh,
+                       (const XT *)L.dinv, b, x, lim);
+        else
+            pdl_launch(k_sell_sor<XT, XT, BT>, grid_for(threads, kSellBlock), kSellBlock, s, s0, s1, L.A.row0,
+                       L.A.nrow, L.A.off, L.A.width, L.A.col, (const XT *)L.A.v, (const XT *)L.dinv, b, x, lim);
         SOLVE_LAUNCHED();
     }
 }
 
 template <class XT, class BT>
 static void residual(const SLevel &L, const BT *b, const XT *x, XT *r, cudaStream_t s) {
-    ProbeScope ps(PROBE_RESIDUAL, sell_bytes(L.A.nnz, sizeof(XT), L.n, 5.0 * sizeof(XT)), s);
+    ProbeScope ps(PROBE_RESIDUAL, sell_bytes(L.A.nnz, value_bytes<XT>(L.A), L.n, 5.0 * sizeof(XT)), s);
     int64_t threads = (int64_t)L.A.nslices * 32;
-    pdl_launch(k_sell_residual<XT, XT, BT>, grid_for(threads, kSellBlock), kSellBlock, s, 
-        L.A.nslices, L.A.row0, L.A.nrow, L.A.off, L.A.width, L.A.col, (const XT *)L.A.v, (const XT *)L.diag, b, x, r);
+    if (L.A.vh)
+        pdl_launch(k_sell_residual<__nv_bfloat16, XT, BT>, grid_for(threads, kSellBlock), kSellBlock, s,
+                   L.A.nslices, L.A.row0, L.A.nrow, L.A.off, L.A.width, L.A.col, (const __nv_bfloat16 *)L.A.vh,
+                   (const XT *)L.diag, b, x, r);
+    else
+        pdl_launch(k_sell_residual<XT, XT, BT>, grid_for(threads, kSellBlock), kSellBlock, s, L.A.nslices,
+                   L.A.row0, L.A.nrow, L.A.off, L.A.width, L.A.col, (const XT *)L.A.v, (const XT *)L.diag, b, x, r);
     SOLVE_LAUNCHED();
 }
 
@@ -646,7 +673,7 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
 }
 
 static void precond_solve_order(vemg_hierarchy *h, const double *r, double *z, int first, cudaStream_t s) {
-    if (h->precision == VEMG_PREC_FP32) precond_t<float>(h, r, z, first, s);
+    if (h->precision != VEMG_PREC_FP64) precond_t<float>(h, r, z, first, s);
     else precond_t<double>(h, r, z, first, s);
 }
 

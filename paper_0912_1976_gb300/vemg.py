@@ -17,7 +17,7 @@ from . import build as _build
 VEMG_OK, VEMG_EINVAL, VEMG_EMESH, VEMG_ENOMEM, VEMG_ENOTCONV, VEMG_EBREAKDOWN, VEMG_ETIMEOUT, VEMG_ECUDA, \
     VEMG_EINTERNAL = range(9)
 VEMG_NEUMANN, VEMG_DIRICHLET_TOP = 0, 1
-VEMG_PREC_FP64, VEMG_PREC_FP32 = 0, 1
+VEMG_PREC_FP64, VEMG_PREC_FP32, VEMG_PREC_BF16 = 0, 1, 2
 VEMG_PRECOND_ADDITIVE, VEMG_PRECOND_VL_SOR, VEMG_PRECOND_SA, VEMG_PRECOND_NONE = 0, 1, 2, 3
 VEMG_CYCLE_PERSISTENT, VEMG_CYCLE_LAUNCHES, VEMG_CYCLE_AUTO = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ENOTCONV", 5: "EBREAKDOWN",
