@@ -39,7 +39,7 @@ PRECS = {"fp64": 0, "fp32": 1, "bf16": 2}
 DTYPES = {"fp64": "f64", "fp32": "f64 outer + f32 preconditioner",
           "bf16": "f64 outer + f32 preconditioner with bf16 operator values"}
 SOR_FINE_DRAM_RATIO = 21.2 / 20.2   # ncu DRAM bytes / algorithmic bytes, finest FP32 colour sweep
-CYCLES = {"persistent": 0, "launches": 1, "auto": 2}
+CYCLES = {"persistent": 0, "launches": 1, "auto": 2, "hybrid": 3}
 
 
 def parse():
@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vemg", choices=["vemg", "reference"])
     ap.add_argument("--precision", default="fp32", choices=list(PRECS))
-    ap.add_argument("--cycle", default="auto", choices=["auto", "persistent", "launches"],
+    ap.add_argument("--cycle", default="auto", choices=["auto", "persistent", "launches", "hybrid"],
                     help="one cooperative kernel per preconditioner application, one kernel per phase, or the "
                          "library's choice by precision")
     ap.add_argument("--precond", default="additive", choices=list(PRECONDS),
@@ -66,6 +66,9 @@ def parse():
                     help="the section 4 study: condition estimates of A and M^-1 A over eps (not a timing run)")
     ap.add_argument("--phases", action="store_true",
                     help="with --case: per-phase profile of the persistent preconditioner kernel")
+    ap.add_argument("--tail-rows", type=int, default=None,
+                    help="levels of at most this many rows (below the finest) run as one single-CTA kernel; "
+                         "default: the library's")
     ap.add_argument("--stream-path", action="store_true",
                     help="with --case: launch the solve's kernels on the stream, not from CUDA graphs")
     ap.add_argument("--rhs", type=int, default=0,
@@ -228,6 +231,7 @@ def workload_config(args, n):
                         f"H0 {w['depth'][1]:g}, z-jitter {w['z_jitter']}, xy-jitter {w['xy_jitter']}, "
                         f"all-Neumann, N(0,1) loads mean-zero, rtol {RTOL:g}",
             "precision": args.precision, "preconditioner": args.precond, "cycle": args.cycle, "rhs_per_step": kr,
+            "tail_rows": args.tail_rows if args.tail_rows is not None else "default",
             "l2": "inputs larger than L2 (A alone 0.39 GB; no flush needed)",
             "parallelism": f"independent problems x{args.gpus}" if args.gpus > 1 else "single GPU"}
 
@@ -235,7 +239,7 @@ def workload_config(args, n):
 # --------------------------------------------------------------------------------------------
 # the GPU path
 
-def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe, persistent=False):
+def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe, cycle="launches"):
     """Time args.steps solves (device-resident inputs), then the same through the host-buffer
     entry point, then (optionally) per-kernel-class probes."""
     nb = len(B)
@@ -313,10 +317,14 @@ def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe, persistent=Fa
                   "h2d_bytes_per_step": 8 * n * kcols, "d2h_bytes_per_step": 8 * n * kcols}
     classes = {}
     if probe and not batched:
-        # the persistent cycle (one kernel per preconditioner application) or, with per-phase
-        # launches, its kernel classes
-        if persistent:
+        # the persistent cycle (one kernel per preconditioner application), the hybrid one (its
+        # finest-level colour sweeps and the cooperative kernel of the coarser levels) or, with
+        # per-phase launches, its kernel classes
+        if cycle == "persistent":
             kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "vcycle": V.VEMG_PROBE_VCYCLE}
+        elif cycle == "hybrid":
+            kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "sor_fine": V.VEMG_PROBE_SOR_FINE,
+                     "vcycle_coarse": V.VEMG_PROBE_VCYCLE}
         else:
             kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "sor_fine": V.VEMG_PROBE_SOR_FINE, "sor_all": V.VEMG_PROBE_SOR,
                      "residual": V.VEMG_PROBE_RESIDUAL}
@@ -406,6 +414,18 @@ def case_phases(args, m, h, V, torch):
     return 0
 
 
+def resolved_cycle(cycle, prec):
+    """The launch structure the library runs for a requested cycle (VEMG_CYCLE_AUTO: one kernel
+    per phase; BF16 values always one kernel per phase)."""
+    if prec == "bf16" or cycle == "auto":
+        return "launches"
+    return cycle
+
+
+def tail_opt(args):
+    return {} if args.tail_rows is None else {"tail_rows": args.tail_rows}
+
+
 def run_case(args):
     """A small case for ncu captures: build the mesh, set up, run two solves."""
     import torch
@@ -417,7 +437,7 @@ def run_case(args):
     A = V.vemg_assemble(vm)
     prec = PRECS[args.precision]
     h = V.vemg_setup(A, vm, V.vemg_default_options(precision=prec, precond=PRECONDS[args.precond],
-                                                   cycle=CYCLES[args.cycle]))
+                                                   cycle=CYCLES[args.cycle], **tail_opt(args)))
     if args.phases:
         return case_phases(args, m, h, V, torch)
     kr = max(args.rhs, 1)
@@ -522,13 +542,12 @@ def main():
         A = V.vemg_assemble(vm)
         h = V.vemg_setup(A, vm, V.vemg_default_options(
             precision=PRECS[prec], precond=PRECONDS[args.precond],
-            cycle=CYCLES[args.cycle]))
+            cycle=CYCLES[args.cycle], **tail_opt(args)))
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
-        # VEMG_CYCLE_AUTO resolves to the persistent kernel for FP64 V-cycles
-        persistent = prec != "bf16" and (args.cycle == "persistent" or (args.cycle == "auto" and prec == "fp64"))
-        r = measure(args, h, B, n, ws, rank, local, dist, V, torch, probe=not args.no_probe, persistent=persistent)
-        r["cycle"] = "persistent" if persistent else "launches"
+        cyc = resolved_cycle(args.cycle, prec)
+        r = measure(args, h, B, n, ws, rank, local, dist, V, torch, probe=not args.no_probe, cycle=cyc)
+        r["cycle"] = cyc
         r["setup_s"] = setup_s
         r["hierarchy_bytes"] = V.vemg_hierarchy_bytes(h)
         res[prec] = r

@@ -64,8 +64,9 @@ extern "C" {
 /* how a preconditioner application is launched */
 #define VEMG_CYCLE_PERSISTENT 0  /* one cooperative kernel runs every phase of the V-cycles */
 #define VEMG_CYCLE_LAUNCHES 1    /* one kernel per phase (colour sweep, residual, transfer) */
-#define VEMG_CYCLE_AUTO 2        /* the faster of the two as measured on GB300: persistent for FP64
-                                    V-cycles, one kernel per phase for FP32 ones */
+#define VEMG_CYCLE_AUTO 2        /* the fastest structure as measured on GB300: one kernel per phase */
+#define VEMG_CYCLE_HYBRID 3      /* one kernel per phase on each chain's finest level, one cooperative
+                                    kernel for the coarser levels of both chains */
 
 /* precision of the preconditioner; the outer Krylov loop is always FP64 */
 #define VEMG_PREC_FP64 0   /* everything FP64, CG outer loop */
@@ -111,6 +112,10 @@ typedef struct vemg_options {
     int precond;      /* VEMG_PRECOND_*. With Dirichlet-top the additive form and SA are the same
                          cycle (SA on A_bar); VL_SOR needs Neumann (VEMG_EINVAL otherwise) */
     int cycle;        /* VEMG_CYCLE_*: same arithmetic, different launch structure */
+    int tail_rows;    /* per-phase cycles: the first level below the finest with at most this many
+                         rows, and every level under it, run as one single-CTA kernel (0: never);
+                         0..65536, default 0 (measured slower than one kernel per phase once the
+                         kernels load their operator rows before waiting on their predecessor) */
 } vemg_options;
 
 typedef struct vemg_info {
@@ -124,7 +129,8 @@ typedef struct vemg_info {
 typedef struct vemg_hierarchy vemg_hierarchy;
 
 /* Fill opts with the paper's parameters (section 6): strength 0.01, omega_p = 2/3, Neumann,
-   FP64, coarse_max = 512, max_levels = 10, the additive preconditioner, VEMG_CYCLE_AUTO. */
+   FP64, coarse_max = 512, max_levels = 10, the additive preconditioner, VEMG_CYCLE_AUTO,
+   tail_rows = 0. */
 void vemg_default_options(vemg_options *opts);
 
 /* Assemble the P1 stiffness matrix A_ij = integral grad N_i . grad N_j in physical coordinates

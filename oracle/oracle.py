@@ -61,7 +61,7 @@ def lib():
         L.or_spmv.argtypes = [C.c_void_p, dp, dp]
         L.or_load.argtypes = [C.c_void_p, dp, dp]
         L.or_vcycle.argtypes = [C.c_void_p, C.c_int, dp, dp]
-        L.or_sa_aggregate.argtypes = [C.c_int, ip, ip, dp, C.c_double, ip]
+        L.or_sa_aggregate.argtypes = [C.c_int, ip, ip, dp, C.c_double, C.c_int, ip]
         L.or_colour.argtypes = [C.c_int, ip, ip, ip]
         L.or_sl_ranks.argtypes = [C.c_int, ip, ip, ip]
         L.or_locate_points.argtypes = [C.c_int, ip, dp, C.c_int, dp, ip, dp]
@@ -206,13 +206,14 @@ def round_bf16(a: float) -> float:
     return lib().or_round_bf16(float(a))
 
 
-def sa_aggregate(A: sp.csr_matrix, theta=THETA):
+def sa_aggregate(A: sp.csr_matrix, theta=THETA, keep_isolated=True):
+    """Aggregates of the rows of A (-1: an isolated row left unaggregated, keep_isolated False)."""
     A = A.tocsr()
     A.sort_indices()
     rp, ci, v = _i32(A.indptr), _i32(A.indices), _f64(A.data)
     agg = np.zeros(A.shape[0], np.int32)
     nagg = lib().or_sa_aggregate(A.shape[0], _p(rp, C.c_int), _p(ci, C.c_int), _p(v, C.c_double), theta,
-                                 _p(agg, C.c_int))
+                                 int(keep_isolated), _p(agg, C.c_int))
     return nagg, agg
 
 

@@ -357,9 +357,14 @@ static int mis2_round(const csr *S, const uint64_t *key, const char *cand, const
    2. every remaining node with a strong neighbour in a phase-1 aggregate joins the aggregate
       of its strongest such neighbour (ties: lowest aggregate id);
    3. the rest are aggregated among themselves by the rule of phase 1 restricted to
-      unaggregated nodes (isolated nodes become singletons).
+      unaggregated nodes.
+   Isolated nodes (no strong coupling) become singleton aggregates when keep_isolated is set
+   (singular chains: every node must keep a coarse representative for P 1 = 1); otherwise they
+   stay unaggregated (agg = -1), as in Vanek, Mandel and Brezina: their prolongator rows are
+   zero and the smoother alone treats them.
    Returns the number of aggregates. */
-int or_sa_aggregate(int n, const int *rp, const int *ci, const double *v, double theta, int *agg) {
+int or_sa_aggregate(int n, const int *rp, const int *ci, const double *v, double theta, int keep_isolated,
+                    int *agg) {
     csr A;
     A.n = n; A.m = n; A.rp = (int *)rp; A.ci = (int *)ci; A.v = (double *)v;
     csr S = strength_graph(&A, theta);
@@ -378,7 +383,7 @@ int or_sa_aggregate(int n, const int *rp, const int *ci, const double *v, double
     for (;;) {
         int any = 0;
         for (int i = 0; i < n; ++i) {
-            int f = agg[i] < 0;
+            int f = agg[i] < 0 && (keep_isolated || S.rp[i + 1] > S.rp[i]);
             for (int k = S.rp[i]; f && k < S.rp[i + 1]; ++k)
                 if (agg[S.ci[k]] >= 0) f = 0;
             cand[i] = (char)f;
@@ -412,7 +417,11 @@ int or_sa_aggregate(int n, const int *rp, const int *ci, const double *v, double
     /* phase 3 */
     for (;;) {
         int any = 0;
-        for (int i = 0; i < n; ++i) { cand[i] = (char)(agg[i] < 0); thr[i] = cand[i]; any |= cand[i]; }
+        for (int i = 0; i < n; ++i) {
+            cand[i] = (char)(agg[i] < 0 && (keep_isolated || S.rp[i + 1] > S.rp[i]));
+            thr[i] = cand[i];
+            any |= cand[i];
+        }
         if (!any) break;
         mis2_round(&S, key, cand, thr, m1, isroot);
         for (int i = 0; i < n; ++i)
@@ -531,6 +540,7 @@ static csr smoothed_prolongator(const csr *A, const int *agg, int nagg, double o
     int *rp = (int *)xcalloc((size_t)n + 1, sizeof(int));
     for (int i = 0; i < n; ++i) {
         int c = 0;
+        if (agg[i] < 0) { rp[i + 1] = rp[i]; continue; }   /* unaggregated: zero row */
         mark[agg[i]] = i; c++;
         for (int k = A->rp[i]; k < A->rp[i + 1]; ++k) {
             int j = A->ci[k];
@@ -547,6 +557,7 @@ static csr smoothed_prolongator(const csr *A, const int *agg, int nagg, double o
     for (int j = 0; j < nagg; ++j) mark[j] = -1;
     for (int i = 0; i < n; ++i) {
         int base = P.rp[i], c = 0, nstrong = 0;
+        if (agg[i] < 0) continue;
         /* filtered diagonal: the dropped (weak) couplings are lumped into it, so that the
            filtered row has the row sum of A's row and P keeps the constants A annihilates */
         double dF = d[i];
@@ -644,8 +655,8 @@ static int chain_build(chain *C, csr A0, int singular, double theta, double omeg
         level *L = &C->lv[C->nlev - 1];
         int n = L->A.n;
         int *agg = (int *)xcalloc((size_t)n, sizeof(int));
-        int nagg = or_sa_aggregate(n, L->A.rp, L->A.ci, L->A.v, theta, agg);
-        if ((long)nagg * 10 > (long)n * 9) { free(agg); break; }
+        int nagg = or_sa_aggregate(n, L->A.rp, L->A.ci, L->A.v, theta, singular, agg);
+        if (nagg == 0 || (long)nagg * 10 > (long)n * 9) { free(agg); break; }
         L->agg = agg;
         L->P = smoothed_prolongator(&L->A, agg, nagg, omega_p, theta);
         L->PT = csr_transpose(&L->P);

@@ -62,6 +62,7 @@ struct BChain {
     bool direct = false;
     int nc = 0;
     const double *G = nullptr;
+    const float *Gf = nullptr;   // FP32 copy (FP32 cycles)
 };
 
 struct CsrP {
@@ -222,12 +223,12 @@ static void bcsr(CsrP A, int nrows, const int *rows, int r0, const VT *dg, const
 
 // x = G b on the coarsest level, one thread per (row, column)
 template <class XT, class BT>
-__global__ void k_bdense(int n, const double *__restrict__ G, const BT *__restrict__ b, XT *__restrict__ x, int K) {
+__global__ void k_bdense(int n, const XT *__restrict__ G, const BT *__restrict__ b, XT *__restrict__ x, int K) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)n * K) return;
     int r = (int)(t >> (__ffs(K) - 1)), c = (int)(t & (K - 1));
-    double s = 0.0;
-    for (int j = 0; j < n; ++j) s += G[(int64_t)r * n + j] * (double)b[(int64_t)j * K + c];
+    XT s = 0;
+    for (int j = 0; j < n; ++j) s += G[(int64_t)r * n + j] * (XT)b[(int64_t)j * K + c];
     x[t] = (XT)s;
 }
 
@@ -249,7 +250,8 @@ static void bvcycle(const BChain &C, BatchWork *W, int ch, int l, const BT *b, X
     if (l == C.nlev - 1) {
         if (C.direct) {
             int64_t t = (int64_t)C.nc * K;
-            k_bdense<XT, BT><<<grid_for(t, 256), 256, 0, s>>>(C.nc, C.G, b, x, K);
+            const XT *G = sizeof(XT) == sizeof(float) ? (const XT *)C.Gf : (const XT *)C.G;
+            k_bdense<XT, BT><<<grid_for(t, 256), 256, 0, s>>>(C.nc, G, b, x, K);
             BATCH_LAUNCHED();
             return;
         }
@@ -802,6 +804,7 @@ static BChain *build_bchain(const Chain &C, bool fp32, Arena &ar, cudaStream_t s
     B->direct = C.direct;
     B->nc = C.nc;
     B->G = C.G;
+    if (C.direct && fp32) B->Gf = (const float *)values(ar, C.G, (int64_t)C.nc * C.nc, true, s);
     for (int l = 0; l < C.nlev; ++l) {
         const Level &L = C.lv[l];
         BLevel &T = B->lv[l];

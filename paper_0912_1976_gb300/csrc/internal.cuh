@@ -186,6 +186,7 @@ struct SChain {
     bool direct = false, singular = false, fp32 = false, is_bar = false;
     int nc = 0;
     double *G = nullptr;           // coarsest dense inverse in solve order
+    float *Gf = nullptr;           // its FP32 copy (FP32 cycles)
     // the coarse tail (levels tail_level.. as one single-CTA kernel, persist.cu); -1: none
     int tail_level = -1, tail_n = 0;
     const void *tail = nullptr;
@@ -198,7 +199,6 @@ struct Chain {
     bool direct = false;    // coarsest level solved by the dense inverse
     int nc = 0;
     double *G = nullptr;    // nc x nc: inverse of the coarsest operator (projected on singular chains)
-    float *Gf = nullptr;
     bool is_bar = false;    // the A_bar chain (its level 0 is the finest smoother level)
 };
 
@@ -244,7 +244,7 @@ struct vemg_hierarchy {
     // CUDA graphs of the solve (built on the first solve)
     vemg::Graphs *graphs = nullptr;
     cudaStream_t side = nullptr;                  // second branch of the preconditioner
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_mid = nullptr, ev_coarse = nullptr;
     unsigned *ctr = nullptr;                      // arrival counters of the block reductions
     vemg::BatchWork *batch = nullptr;             // multi-right-hand-side work (batch.cu)
     vemg::Persist *persist = nullptr;             // the persistent preconditioner program (persist.cu)
@@ -263,6 +263,7 @@ inline const Chain &the_chain(const vemg_hierarchy *h) { return h->bc == VEMG_DI
 void build_persist(vemg_hierarchy *h, cudaStream_t s);
 void release_persist(vemg_hierarchy *h);
 void launch_persist(vemg_hierarchy *h, const double *r, cudaStream_t s);
+bool persist_coarse_only(const vemg_hierarchy *h);   // the program holds levels >= 1 only (hybrid)
 void persist_reset(vemg_hierarchy *h, cudaStream_t s);
 double persist_bytes(const vemg_hierarchy *h);
 const int *persist_err(const vemg_hierarchy *h);

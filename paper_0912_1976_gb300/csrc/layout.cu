@@ -169,6 +169,11 @@ __global__ void k_permute_dense(int n, const int *__restrict__ s2n, const double
     Gs[t] = G[(int64_t)s2n[a] * n + s2n[b]];
 }
 
+__global__ void k_to_float(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
 // b = a rounded to BF16 (nearest, ties to even); a is overwritten by the same value in FP32
 __global__ void k_f2bf(int64_t n, float *__restrict__ a, __nv_bfloat16 *__restrict__ b) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -238,6 +243,11 @@ static void layout_chain(Arena &ar, const Chain &C, SChain &S, bool fp32, cudaSt
         S.G = ar.alloc<double>((int64_t)n * n);
         k_permute_dense<<<grid_for((int64_t)n * n, 256), 256, 0, s>>>(n, C.lv[C.nlev - 1].crow, C.G, S.G);
         VEMG_CHECK_LAUNCH();
+        if (fp32) {   // FP32 cycles apply the dense inverse in FP32
+            S.Gf = ar.alloc<float>((int64_t)n * n);
+            k_to_float<<<grid_for((int64_t)n * n, 256), 256, 0, s>>>((int64_t)n * n, S.G, S.Gf);
+            VEMG_CHECK_LAUNCH();
+        }
     }
 }
 
@@ -253,10 +263,6 @@ __global__ void k_compose(int n, const int *__restrict__ a, const int *__restric
     if (i < n) out[i] = a[off + b[i]];
 }
 
-__global__ void k_to_float(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (float)a[i];
-}
 
 __global__ void k_iota(int n, int *out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -63,6 +63,7 @@ struct Persist {
     double bytes = 0.0;            // algorithmic bytes of one application
     int nphases = 0;
     bool fp32 = false;
+    bool coarse = false;           // levels >= 1 of the chains only (the hybrid structure)
     unsigned long long *cycles = nullptr;   // device: per phase, SM clock cycles summed over launches
     std::vector<int> op, level, group;      // host copies for profiles
 };
@@ -264,12 +265,12 @@ __device__ void run_phase(const PPhase &p, const double *__restrict__ r, int gw,
         }
         return;
     }
-    if (p.op == PH_DENSE) {   // x = G b, one warp per row, FP64 accumulation
-        const double *G = (const double *)p.v;
+    if (p.op == PH_DENSE) {   // x = G b, one warp per row, G and sums in XT
+        const XT *G = (const XT *)p.v;
         XT *x = (XT *)p.x;
         for (int row = gw; row < p.n; row += nw) {
-            double s = 0.0;
-            for (int k = lane; k < p.n; k += 32) s += __ldg(G + (int64_t)row * p.n + k) * (double)rhs<XT>(p, r, k);
+            XT s = 0;
+            for (int k = lane; k < p.n; k += 32) s += __ldg(G + (int64_t)row * p.n + k) * rhs<XT>(p, r, k);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) stcg(x + row, (XT)s);
@@ -470,12 +471,12 @@ struct Builder {
                 PPhase p{};
                 p.op = PH_DENSE;
                 p.n = C.nc;
-                p.v = C.G;
+                p.v = C.fp32 ? (const void *)C.Gf : (const void *)C.G;
                 set_b(p, b, outer_off);
                 p.x = x;
                 p.level = l;
                 ph.push_back(p);
-                bytes += 8.0 * C.nc * (double)C.nc + 2.0 * xs * C.nc;
+                bytes += xs * C.nc * (double)C.nc + 2.0 * xs * C.nc;
                 return;
             }
             sweep(L, b, outer_off, x, true, true);
@@ -512,21 +513,35 @@ static int max_blocks_per_sm() {
 void build_persist(vemg_hierarchy *h, cudaStream_t s) {
     if (h->persist) return;
     const bool fp32 = h->precision != VEMG_PREC_FP64;
-    const bool two = !single_chain(h);
+    const bool coarse = h->opts.cycle == VEMG_CYCLE_HYBRID;
+    bool two = !single_chain(h);
     Builder B(h->arena, s);
     B.xs = fp32 ? 4 : 8;
     std::vector<int2> ranges;   // phase ranges per group
-    if (two) {
-        const SChain &S = h->ssurf;
-        int p0 = (int)B.ph.size();
-        PPhase p = B.sell_phase(PH_RESTRICT_F64, h->ETs, 0, h->ETs.nslices);
-        p.x = S.lv[0].b;
-        B.ph.push_back(p);
-        B.bytes += (double)h->ETs.nnz * 12.0 + (double)h->ETs.n * B.xs + 8.0 * h->n;
-        B.vcycle(S, 0, S.lv[0].b, -1, S.lv[0].x);
-        ranges.push_back({p0, (int)B.ph.size()});
-    }
-    {
+    if (coarse) {
+        // levels >= 1 of each chain that has them; the finest levels run one kernel per phase
+        const SChain *cs[2] = {two ? &h->ssurf : nullptr, &h->sbar};
+        int with = 0;
+        for (const SChain *C : cs) {
+            if (!C || C->nlev < 2) continue;
+            int p0 = (int)B.ph.size();
+            B.vcycle(*C, 1, C->lv[1].b, -1, C->lv[1].x);
+            ranges.push_back({p0, (int)B.ph.size()});
+            ++with;
+        }
+        if (with == 0) return;   // no coarse levels: the hybrid cycle is the per-phase one
+        two = with == 2;
+    } else {
+        if (two) {
+            const SChain &S = h->ssurf;
+            int p0 = (int)B.ph.size();
+            PPhase p = B.sell_phase(PH_RESTRICT_F64, h->ETs, 0, h->ETs.nslices);
+            p.x = S.lv[0].b;
+            B.ph.push_back(p);
+            B.bytes += (double)h->ETs.nnz * 12.0 + (double)h->ETs.n * B.xs + 8.0 * h->n;
+            B.vcycle(S, 0, S.lv[0].b, -1, S.lv[0].x);
+            ranges.push_back({p0, (int)B.ph.size()});
+        }
         int p0 = (int)B.ph.size();
         B.vcycle(h->sbar, 0, nullptr, two ? h->mtop : 0, h->sbar.lv[0].x);
         ranges.push_back({p0, (int)B.ph.size()});
@@ -572,6 +587,7 @@ void build_persist(vemg_hierarchy *h, cudaStream_t s) {
         P->grid = grid;
         P->bytes = B.bytes;
         P->fp32 = fp32;
+        P->coarse = coarse;
     } catch (...) {
         delete P;
         throw;
@@ -579,17 +595,15 @@ void build_persist(vemg_hierarchy *h, cudaStream_t s) {
     h->persist = P;
 }
 
-// Coarse tails: the first level below the finest with at most kTailRows rows starts a tail. A
-// colour of such a level has at most ~1,000 rows, about one row per thread of the tail CTA, so a
-// phase costs one memory round trip plus a CTA barrier instead of a kernel launch. One SM's
-// bandwidth bounds the size: with 32,768 rows the tail was slower than the launches.
-static constexpr int kTailRows = 12288;
-
-static void build_tail(Arena &ar, SChain &C, bool fp32, cudaStream_t s) {
+// Coarse tails: the first level below the finest with at most tail_rows rows starts a tail. A
+// colour of such a level has about one row per thread of the tail CTA, so a phase costs one
+// memory round trip plus a CTA barrier instead of a kernel launch; one SM's bandwidth and FP
+// rate bound the size that pays.
+static void build_tail(Arena &ar, SChain &C, bool fp32, int tail_rows, cudaStream_t s) {
     C.tail_level = -1;
     int l0 = -1;
     for (int l = 1; l < C.nlev; ++l)
-        if (C.lv[l].n <= kTailRows) {
+        if (C.lv[l].n <= tail_rows) {
             l0 = l;
             break;
         }
@@ -608,8 +622,8 @@ static void build_tail(Arena &ar, SChain &C, bool fp32, cudaStream_t s) {
 void build_tails(vemg_hierarchy *h, cudaStream_t s) {
     const bool fp32 = h->precision != VEMG_PREC_FP64;
     if (h->precond == VEMG_PRECOND_NONE) return;
-    if (!single_chain(h)) build_tail(h->arena, h->ssurf, fp32, s);
-    build_tail(h->arena, h->sbar, fp32, s);
+    if (!single_chain(h)) build_tail(h->arena, h->ssurf, fp32, h->opts.tail_rows, s);
+    build_tail(h->arena, h->sbar, fp32, h->opts.tail_rows, s);
 }
 
 void launch_tail(const SChain &C, cudaStream_t s) {
@@ -626,6 +640,7 @@ void release_persist(vemg_hierarchy *h) {
 }
 
 double persist_bytes(const vemg_hierarchy *h) { return h->persist ? h->persist->bytes : 0.0; }
+bool persist_coarse_only(const vemg_hierarchy *h) { return h->persist && h->persist->coarse; }
 const int *persist_err(const vemg_hierarchy *h) { return h->persist ? h->persist->err : nullptr; }
 
 // reset the barrier words and the error word after a failed application

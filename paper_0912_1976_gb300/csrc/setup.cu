@@ -884,11 +884,13 @@ __global__ void k_agg_keys(int n, const int *__restrict__ srp, uint64_t *key) {
 }
 
 // phase 1 candidates: unaggregated with an unaggregated strong neighbourhood
+// keep_isolated == 0: a node without strong couplings is never a candidate and stays
+// unaggregated (zero prolongator row)
 __global__ void k_phase1_cand(int n, const int *__restrict__ srp, const int *__restrict__ sci,
-                              const int *__restrict__ agg, char *cand, char *thr, int *any) {
+                              const int *__restrict__ agg, int keep_isolated, char *cand, char *thr, int *any) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    bool f = agg[i] < 0;
+    bool f = agg[i] < 0 && (keep_isolated || srp[i + 1] > srp[i]);
     for (int k = srp[i]; f && k < srp[i + 1]; ++k)
         if (agg[sci[k]] >= 0) f = false;
     cand[i] = f;
@@ -896,10 +898,11 @@ __global__ void k_phase1_cand(int n, const int *__restrict__ srp, const int *__r
     if (f) *any = 1;
 }
 
-__global__ void k_phase3_cand(int n, const int *__restrict__ agg, char *cand, char *thr, int *any) {
+__global__ void k_phase3_cand(int n, const int *__restrict__ srp, const int *__restrict__ agg, int keep_isolated,
+                              char *cand, char *thr, int *any) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    bool f = agg[i] < 0;
+    bool f = agg[i] < 0 && (keep_isolated || srp[i + 1] > srp[i]);
     cand[i] = f;
     thr[i] = f;
     if (f) *any = 1;
@@ -979,8 +982,11 @@ static int read_int(const int *d, cudaStream_t s) {
 }
 
 // Vanek's three aggregation phases made round-synchronous (see the oracle for the rule).
+// Isolated nodes (no strong coupling) become singletons when keep_isolated is set (singular
+// chains, where P 1 = 1 needs every node), else they stay unaggregated (agg = -1).
 // Returns the number of aggregates; agg is allocated in the arena.
-static int sa_aggregate(Arena &ar, const DCsr &A, const double *d, double theta, int **agg_out, cudaStream_t s) {
+static int sa_aggregate(Arena &ar, const DCsr &A, const double *d, double theta, bool keep_isolated, int **agg_out,
+                        cudaStream_t s) {
     int n = A.n;
     Scratch<int> slen(n);
     k_strong_len<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, d, theta, slen);
@@ -1003,9 +1009,9 @@ static int sa_aggregate(Arena &ar, const DCsr &A, const double *d, double theta,
         for (;;) {
             VEMG_CHECK_CUDA(cudaMemsetAsync(any, 0, sizeof(int), s));
             if (phase == 1)
-                k_phase1_cand<<<grid_for(n, 256), 256, 0, s>>>(n, srp, sci, agg, cand, thr, any);
+                k_phase1_cand<<<grid_for(n, 256), 256, 0, s>>>(n, srp, sci, agg, keep_isolated, cand, thr, any);
             else
-                k_phase3_cand<<<grid_for(n, 256), 256, 0, s>>>(n, agg, cand, thr, any);
+                k_phase3_cand<<<grid_for(n, 256), 256, 0, s>>>(n, srp, agg, keep_isolated, cand, thr, any);
             VEMG_CHECK_LAUNCH();
             if (!read_int(any, s)) break;
             k_mis_m1<<<grid_for(n, 256), 256, 0, s>>>(n, srp, sci, key, cand, thr, m1);
@@ -1032,12 +1038,17 @@ static int sa_aggregate(Arena &ar, const DCsr &A, const double *d, double theta,
 // smoothed prolongator P = (I - omega (D^F)^-1 A^F) P_tent with Vanek's filtered matrix:
 // weak off-diagonal entries dropped and lumped into the diagonal, so that each filtered row keeps
 // the row sum of A and P keeps the constants (section 6: omega = 2/3). A row with no strong
-// coupling, or a non-positive filtered diagonal, keeps its tentative row.
+// coupling, or a non-positive filtered diagonal, keeps its tentative row; an unaggregated row is
+// empty.
 __global__ void k_prolong_len(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                               const double *__restrict__ v, const double *__restrict__ d, double theta,
                               const int *__restrict__ agg, int *len, int *err) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (agg[i] < 0) {
+        len[i] = 0;
+        return;
+    }
     int u[kMaxRowUnique];
     int c = 0;
     c = insert_unique(u, c, kMaxRowUnique, agg[i]);
@@ -1055,7 +1066,7 @@ __global__ void k_prolong_fill(int n, const int *__restrict__ rp, const int *__r
                                double omega, const int *__restrict__ agg, const int *__restrict__ prp, int *pci,
                                double *pv) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || agg[i] < 0) return;
     int lo = prp[i], hi = prp[i + 1];
     int c = 0;
     int *u = pci + lo;
@@ -1403,8 +1414,8 @@ static void build_chain(Arena &ar, Chain &C, DCsr A0, bool singular, const vemg_
         VEMG_CHECK_LAUNCH();
         int *agg = nullptr;
         Arena tmp;
-        int nagg = sa_aggregate(tmp, L.A, d, o.strength, &agg, s);
-        if ((int64_t)nagg * 10 > (int64_t)n * 9) {
+        int nagg = sa_aggregate(tmp, L.A, d, o.strength, singular, &agg, s);
+        if (nagg == 0 || (int64_t)nagg * 10 > (int64_t)n * 9) {
             tmp.release();
             break;
         }

@@ -106,9 +106,7 @@ static double sell_bytes(int64_t nnz, double vb, int64_t rows, double per_row) {
 // ------------------------------------------------------------------------------------------
 // sliced-ELL kernels
 
-// Dot product of one sliced-ELL row with x: entries are loaded kU at a time (column indices and
-// values first, then the gathers), so that a row costs two dependent memory round trips per kU
-// entries instead of two per entry. lim >= 0 skips columns >= lim.
+// entries of a sliced-ELL row loaded per chunk (before their gathers)
 static constexpr int kU = 16;
 
 // BF16 values widen to FP32 before they meet the vector; FP32 and FP64 values pass through
@@ -116,11 +114,37 @@ __device__ __forceinline__ float float_or_self(__nv_bfloat16 a) { return __bfloa
 __device__ __forceinline__ float float_or_self(float a) { return a; }
 __device__ __forceinline__ double float_or_self(double a) { return a; }
 
+// The first kU entries of a sliced-ELL row (column indices and values), loaded before the
+// kernel waits for its predecessor: the operators are setup data that no solve kernel writes,
+// so these loads overlap the previous kernel and only the gathers of x remain after the wait.
+template <class VT>
+struct RowHead {
+    int c[kU];
+    VT a[kU];
+};
+
+template <class VT>
+__device__ __forceinline__ void load_head(RowHead<VT> &h, const int *__restrict__ col, const VT *__restrict__ v, int o,
+                                          int w) {
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+        h.c[u] = u < w ? __ldg(col + o + 32 * u) : 0;
+        h.a[u] = u < w ? __ldg(v + o + 32 * u) : VT{};
+    }
+}
+
+// Dot product of one sliced-ELL row with x: the head's entries, then the rest of the row kU
+// entries at a time (column indices and values first, then the gathers), so that a row costs
+// two dependent memory round trips per kU entries instead of two per entry. lim >= 0 skips
+// columns >= lim.
 template <class VT, class XT, class AT>
-__device__ __forceinline__ AT sell_row(const int *__restrict__ col, const VT *__restrict__ v, int o, int w,
-                                       const XT *x, int lim) {
+__device__ __forceinline__ AT sell_row(const RowHead<VT> &h, const int *__restrict__ col, const VT *__restrict__ v,
+                                       int o, int w, const XT *x, int lim) {
     AT acc = 0;
-    for (int k0 = 0; k0 < w; k0 += kU) {
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+        if (u < w && (lim < 0 || h.c[u] < lim)) acc += (AT)(float_or_self(h.a[u])) * (AT)x[h.c[u]];
+    for (int k0 = kU; k0 < w; k0 += kU) {
         int c[kU];
         VT a[kU];
 #pragma unroll
@@ -136,6 +160,14 @@ __device__ __forceinline__ AT sell_row(const int *__restrict__ col, const VT *__
     return acc;
 }
 
+template <class VT, class XT, class AT>
+__device__ __forceinline__ AT sell_row(const int *__restrict__ col, const VT *__restrict__ v, int o, int w,
+                                       const XT *x, int lim) {
+    RowHead<VT> h;
+    load_head(h, col, v, o, w);
+    return sell_row<VT, XT, AT>(h, col, v, o, w, x, lim);
+}
+
 // y = A x (add: y += A x) over the slices [s0, s1); accumulation in AT
 template <class VT, class XT, class YT, class AT>
 __global__ void __launch_bounds__(kSellBlock) k_sell_spmv(int s0, int s1, const int *__restrict__ row0,
@@ -143,12 +175,20 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_spmv(int s0, int s1, const 
                                                           const int *__restrict__ width, const int *__restrict__ col,
                                                           const VT *__restrict__ v, const XT *__restrict__ x,
                                                           YT *__restrict__ y, int add) {
-    pdl_begin();
     int s = s0 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
-    if (s >= s1 || lane >= nrow[s]) return;
-    AT acc = sell_row<VT, XT, AT>(col, v, off[s] + lane, width[s], x, -1);
-    int r = row0[s] + lane;
+    const bool active = s < s1 && lane < nrow[s];
+    RowHead<VT> h;
+    int o = 0, w = 0, r = 0;
+    if (active) {
+        o = off[s] + lane;
+        w = width[s];
+        r = row0[s] + lane;
+        load_head(h, col, v, o, w);
+    }
+    pdl_begin();
+    if (!active) return;
+    AT acc = sell_row<VT, XT, AT>(h, col, v, o, w, x, -1);
     y[r] = add ? (YT)((AT)y[r] + acc) : (YT)acc;
 }
 
@@ -161,13 +201,23 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_sor(int s0, int s1, const i
                                                          const int *__restrict__ width, const int *__restrict__ col,
                                                          const VT *__restrict__ v, const XT *__restrict__ dinv,
                                                          const BT *__restrict__ b, XT *x, int lim) {
-    pdl_begin();
     int s = s0 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
-    if (s >= s1 || lane >= nrow[s]) return;
-    int r = row0[s] + lane;
-    XT acc = lim == 0 ? (XT)0 : sell_row<VT, XT, XT>(col, v, off[s] + lane, width[s], x, lim);
-    x[r] = ((XT)b[r] - acc) * (XT)dinv[r];
+    const bool active = s < s1 && lane < nrow[s];
+    RowHead<VT> h;
+    int o = 0, w = 0, r = 0;
+    XT di = 0;
+    if (active) {
+        o = off[s] + lane;
+        w = lim == 0 ? 0 : width[s];
+        r = row0[s] + lane;
+        di = dinv[r];
+        load_head(h, col, v, o, w);
+    }
+    pdl_begin();
+    if (!active) return;
+    XT acc = sell_row<VT, XT, XT>(h, col, v, o, w, x, lim);
+    x[r] = ((XT)b[r] - acc) * di;
 }
 
 // r = b - D x - (A - D) x over all slices
@@ -178,23 +228,34 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_residual(int nsl, const int
                                                               const VT *__restrict__ v, const XT *__restrict__ diag,
                                                               const BT *__restrict__ b, const XT *__restrict__ x,
                                                               XT *__restrict__ r) {
-    pdl_begin();
     int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
-    if (s >= nsl || lane >= nrow[s]) return;
-    int i = row0[s] + lane;
-    XT acc = (XT)diag[i] * x[i] + sell_row<VT, XT, XT>(col, v, off[s] + lane, width[s], x, -1);
+    const bool active = s < nsl && lane < nrow[s];
+    RowHead<VT> h;
+    int o = 0, w = 0, i = 0;
+    XT dg = 0;
+    if (active) {
+        o = off[s] + lane;
+        w = width[s];
+        i = row0[s] + lane;
+        dg = diag[i];
+        load_head(h, col, v, o, w);
+    }
+    pdl_begin();
+    if (!active) return;
+    XT acc = dg * x[i] + sell_row<VT, XT, XT>(h, col, v, o, w, x, -1);
     r[i] = (XT)b[i] - acc;
 }
 
-// x = G b for the dense coarsest inverse (one warp per row, FP64 accumulation)
+// x = G b for the dense coarsest inverse (one warp per row; G and the sums in the cycle's
+// precision)
 template <class XT, class BT>
-__global__ void k_dense_mv(int n, const double *__restrict__ Gm, const BT *__restrict__ b, XT *__restrict__ x) {
+__global__ void k_dense_mv(int n, const XT *__restrict__ Gm, const BT *__restrict__ b, XT *__restrict__ x) {
     pdl_begin();
     int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
     if (row >= n) return;
-    double s = 0.0;
-    for (int k = lane; k < n; k += 32) s += Gm[(int64_t)row * n + k] * (double)b[k];
+    XT s = 0;
+    for (int k = lane; k < n; k += 32) s += Gm[(int64_t)row * n + k] * (XT)b[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) x[row] = (XT)s;
@@ -275,7 +336,8 @@ static void vcycle_level(const SChain &C, int l, const BT *b, XT *x, cudaStream_
     }
     if (l == C.nlev - 1) {
         if (C.direct) {
-            pdl_launch(k_dense_mv<XT, BT>, grid_for(C.nc, 8), 256, s, C.nc, C.G, b, x);
+            const XT *G = sizeof(XT) == sizeof(float) ? (const XT *)C.Gf : (const XT *)C.G;
+            pdl_launch(k_dense_mv<XT, BT>, grid_for(C.nc, 8), 256, s, C.nc, G, b, x);
             SOLVE_LAUNCHED();
             return;
         }
@@ -291,6 +353,24 @@ static void vcycle_level(const SChain &C, int l, const BT *b, XT *x, cudaStream_
     vcycle_level<XT, XT>(C, l + 1, (const XT *)N.b, (XT *)N.x, s);
     sell_spmv<XT, XT, XT, XT>(L.P, (const XT *)N.x, x, 1, s);
     sor_sweep<XT, BT>(L, b, x, false, false, fine, s);
+}
+
+// The finest level of a V-cycle split around its coarse correction (the hybrid launch
+// structure): down = pre-smoothing, residual, restriction into level 1; up = prolongation of
+// level 1's x and post-smoothing. The same launches as vcycle_level's, in the same order.
+template <class XT, class BT>
+static void vcycle_down(const SChain &C, const BT *b, XT *x, cudaStream_t s) {
+    const SLevel &L = C.lv[0];
+    sor_sweep<XT, BT>(L, b, x, true, true, C.is_bar, s);
+    residual<XT, BT>(L, b, x, (XT *)L.r, s);
+    sell_spmv<XT, XT, XT, XT>(L.PT, (const XT *)L.r, (XT *)C.lv[1].b, 0, s);
+}
+
+template <class XT, class BT>
+static void vcycle_up(const SChain &C, const BT *b, XT *x, cudaStream_t s) {
+    const SLevel &L = C.lv[0];
+    sell_spmv<XT, XT, XT, XT>(L.P, (const XT *)C.lv[1].x, x, 1, s);
+    sor_sweep<XT, BT>(L, b, x, false, false, C.is_bar, s);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -639,8 +719,39 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
     const int pk = h->probe.kind;
     const bool persist = h->persist && pk != PROBE_SOR && pk != PROBE_SOR_FINE && pk != PROBE_RESIDUAL;
     const bool none = h->precond == VEMG_PRECOND_NONE;
+    const bool hybrid = persist && persist_coarse_only(h);
     if (none) {
         // no preconditioner (plain CG): z = r, formed by k_combine below
+    } else if (hybrid) {
+        // finest levels one kernel per phase (surface on the side stream), the coarser levels of
+        // both chains in one cooperative kernel between the two halves of the finest levels
+        const SChain &S = h->ssurf;
+        const bool sc = two && S.nlev >= 2, bc = B.nlev >= 2;
+        if (two) {
+            VEMG_CHECK_CUDA(cudaEventRecord(h->ev_fork, s));
+            VEMG_CHECK_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+            sell_spmv<double, double, XT, double>(h->ETs, r, (XT *)S.lv[0].b, 0, h->side);
+            if (sc) vcycle_down<XT, XT>(S, (const XT *)S.lv[0].b, (XT *)S.lv[0].x, h->side);
+            else vcycle_level<XT, XT>(S, 0, (const XT *)S.lv[0].b, (XT *)S.lv[0].x, h->side);
+            VEMG_CHECK_CUDA(cudaEventRecord(h->ev_mid, h->side));
+            ys = (const XT *)S.lv[0].x;
+        }
+        if (bc) vcycle_down<XT, double>(B, r + mt, (XT *)B.lv[0].x, s);
+        else vcycle_level<XT, double>(B, 0, r + mt, (XT *)B.lv[0].x, s);
+        if (two) VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_mid, 0));
+        {
+            ProbeScope ps(PROBE_VCYCLE, persist_bytes(h), s);
+            launch_persist(h, r, s);
+            SOLVE_LAUNCHED();
+        }
+        if (two) {
+            VEMG_CHECK_CUDA(cudaEventRecord(h->ev_coarse, s));
+            VEMG_CHECK_CUDA(cudaStreamWaitEvent(h->side, h->ev_coarse, 0));
+            if (sc) vcycle_up<XT, XT>(S, (const XT *)S.lv[0].b, (XT *)S.lv[0].x, h->side);
+            VEMG_CHECK_CUDA(cudaEventRecord(h->ev_join, h->side));
+        }
+        if (bc) vcycle_up<XT, double>(B, r + mt, (XT *)B.lv[0].x, s);
+        if (two) VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
     } else if (persist) {
         // both branches (or the single chain) in one cooperative kernel
         {
@@ -659,7 +770,7 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_join, h->side));
         ys = (const XT *)S.lv[0].x;
     }
-    if (!persist && !none) {
+    if (!persist && !none) {   // one kernel per phase
         // additive smoother: one V-cycle on A_bar with the trailing part of r
         vcycle_level<XT, double>(B, 0, r + mt, (XT *)B.lv[0].x, s);
         if (two) VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
@@ -847,8 +958,10 @@ void release_graphs(vemg_hierarchy *h) {
     if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_mid) cudaEventDestroy(h->ev_mid);
+    if (h->ev_coarse) cudaEventDestroy(h->ev_coarse);
     h->side = nullptr;
-    h->ev_fork = h->ev_join = nullptr;
+    h->ev_fork = h->ev_join = h->ev_mid = h->ev_coarse = nullptr;
 }
 
 void prepare_solve(vemg_hierarchy *h, cudaStream_t s) {
@@ -873,8 +986,12 @@ void prepare_solve(vemg_hierarchy *h, cudaStream_t s) {
     VEMG_CHECK_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     VEMG_CHECK_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     VEMG_CHECK_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    VEMG_CHECK_CUDA(cudaEventCreateWithFlags(&h->ev_mid, cudaEventDisableTiming));
+    VEMG_CHECK_CUDA(cudaEventCreateWithFlags(&h->ev_coarse, cudaEventDisableTiming));
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
-    if (h->opts.cycle == VEMG_CYCLE_PERSISTENT && h->precond != VEMG_PRECOND_NONE) build_persist(h, s);
+    if ((h->opts.cycle == VEMG_CYCLE_PERSISTENT || h->opts.cycle == VEMG_CYCLE_HYBRID) &&
+        h->precond != VEMG_PRECOND_NONE)
+        build_persist(h, s);
     build_tails(h, s);
 }
 

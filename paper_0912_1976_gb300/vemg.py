@@ -19,7 +19,7 @@ VEMG_OK, VEMG_EINVAL, VEMG_EMESH, VEMG_ENOMEM, VEMG_ENOTCONV, VEMG_EBREAKDOWN, V
 VEMG_NEUMANN, VEMG_DIRICHLET_TOP = 0, 1
 VEMG_PREC_FP64, VEMG_PREC_FP32, VEMG_PREC_BF16 = 0, 1, 2
 VEMG_PRECOND_ADDITIVE, VEMG_PRECOND_VL_SOR, VEMG_PRECOND_SA, VEMG_PRECOND_NONE = 0, 1, 2, 3
-VEMG_CYCLE_PERSISTENT, VEMG_CYCLE_LAUNCHES, VEMG_CYCLE_AUTO = 0, 1, 2
+VEMG_CYCLE_PERSISTENT, VEMG_CYCLE_LAUNCHES, VEMG_CYCLE_AUTO, VEMG_CYCLE_HYBRID = 0, 1, 2, 3
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ENOTCONV", 5: "EBREAKDOWN",
                 6: "ETIMEOUT", 7: "ECUDA", 8: "EINTERNAL"}
 
@@ -37,7 +37,7 @@ class vemg_csr(C.Structure):
 
 class vemg_options(C.Structure):
     _fields_ = [("bc", C.c_int), ("precision", C.c_int), ("strength", C.c_double), ("omega_p", C.c_double),
-                ("coarse_max", C.c_int), ("max_levels", C.c_int), ("precond", C.c_int), ("cycle", C.c_int)]
+                ("coarse_max", C.c_int), ("max_levels", C.c_int), ("precond", C.c_int), ("cycle", C.c_int), ("tail_rows", C.c_int)]
 
 
 class vemg_info(C.Structure):

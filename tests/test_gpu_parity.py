@@ -247,14 +247,17 @@ def test_graph_and_stream_paths_agree():
 # the two launch structures of one preconditioner application: one persistent cooperative
 # kernel (default) and one kernel per phase; the same arithmetic row by row
 
+@pytest.mark.parametrize("cycle", [V.VEMG_CYCLE_PERSISTENT, V.VEMG_CYCLE_HYBRID])
 @pytest.mark.parametrize("precision", [V.VEMG_PREC_FP64, V.VEMG_PREC_FP32])
 @pytest.mark.parametrize("name,bc", [("zjit24", V.VEMG_NEUMANN), ("zjit64", V.VEMG_NEUMANN),
                                      ("xyjit20", V.VEMG_NEUMANN), ("zjit24", V.VEMG_DIRICHLET_TOP)])
-def test_persistent_and_per_phase_cycles_agree(name, bc, precision):
+def test_persistent_and_per_phase_cycles_agree(name, bc, precision, cycle):
+    """The cooperative kernel over every phase (persistent) or over the levels below the finest
+    (hybrid) against one kernel per phase."""
     m = CASES[name]()
     vm = V.Mesh.from_inputs(m)
     A = V.vemg_assemble(vm)
-    hp = V.vemg_setup(A, vm, V.vemg_default_options(bc=bc, precision=precision, cycle=V.VEMG_CYCLE_PERSISTENT))
+    hp = V.vemg_setup(A, vm, V.vemg_default_options(bc=bc, precision=precision, cycle=cycle))
     hl = V.vemg_setup(A, vm, V.vemg_default_options(bc=bc, precision=precision, cycle=V.VEMG_CYCLE_LAUNCHES))
     # the single steps work in the internal order of the unknowns (the non-top nodes for
     # Dirichlet-top): compare those entries
@@ -271,6 +274,30 @@ def test_persistent_and_per_phase_cycles_agree(name, bc, precision):
     assert (xp - xl).norm().item() <= (1e-10 if precision == V.VEMG_PREC_FP64 else 1e-7) * xl.norm().item()
     # the eps = 1e-4 mesh has a true-residual floor near 3e-8 (round-off, section 6)
     assert ip["true_relres"] <= max(2e-9, 2.0 * il["true_relres"])
+
+
+@pytest.mark.parametrize("precision", [V.VEMG_PREC_FP64, V.VEMG_PREC_FP32])
+@pytest.mark.parametrize("name,bc", [("zjit64", V.VEMG_NEUMANN), ("zjit24", V.VEMG_DIRICHLET_TOP)])
+def test_single_cta_tail_and_per_phase_cycles_agree(name, bc, precision):
+    """Levels of at most tail_rows rows run in one single-CTA kernel: the same arithmetic row by
+    row as one kernel per phase."""
+    m = CASES[name]()
+    vm = V.Mesh.from_inputs(m)
+    A = V.vemg_assemble(vm)
+    ht = V.vemg_setup(A, vm, V.vemg_default_options(bc=bc, precision=precision, cycle=V.VEMG_CYCLE_LAUNCHES,
+                                                    tail_rows=12288))
+    hl = V.vemg_setup(A, vm, V.vemg_default_options(bc=bc, precision=precision, cycle=V.VEMG_CYCLE_LAUNCHES,
+                                                    tail_rows=0))
+    nu = m.n - (V.vemg_get_size(ht, "mtop") if bc == V.VEMG_DIRICHLET_TOP else 0)
+    r = torch.from_numpy(np.random.default_rng(6).standard_normal(nu)).cuda()
+    zt, zl = V.vemg_precond(ht, r), V.vemg_precond(hl, r)
+    tol = 1e-12 if precision == V.VEMG_PREC_FP64 else 1e-5
+    assert (zt - zl).norm().item() <= tol * zl.norm().item()
+    b = torch.from_numpy(I.normal_loads(m.n, 33)).cuda()
+    xt, it = V.vemg_solve(ht, b, rtol=1e-9)
+    xl, il = V.vemg_solve(hl, b, rtol=1e-9)
+    assert it["status"] == il["status"] == "OK"
+    assert abs(it["iters"] - il["iters"]) <= (0 if precision == V.VEMG_PREC_FP64 else 1)
 
 
 def test_bounded_barrier_wait_gives_up_and_context_survives():

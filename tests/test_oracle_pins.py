@@ -305,6 +305,44 @@ def test_weak_couplings_never_aggregate():
     assert set(agg[:n]).isdisjoint(set(agg[n:]))
 
 
+def test_isolated_nodes_unaggregated_unless_kept():
+    """A node with no strong coupling gets no coarse unknown on non-singular chains (Vanek, Mandel
+    and Brezina): it stays unaggregated, its prolongator row is zero. Singular chains keep it as
+    a singleton so that P 1 = 1."""
+    n = 10
+    L = _lap1d(n).tolil()
+    A = sp.block_diag([L, sp.diags([4.0, 5.0])]).tolil()
+    A[0, n] = A[n, 0] = -0.001          # weak: below 0.01 sqrt(A_ii A_jj)
+    A = A.tocsr()
+    nagg, agg = O.sa_aggregate(A, keep_isolated=False)
+    assert agg[n] == -1 and agg[n + 1] == -1 and np.all(agg[:n] >= 0)
+    assert sorted(set(agg[:n].tolist())) == list(range(nagg))
+    nagg1, agg1 = O.sa_aggregate(A, keep_isolated=True)
+    assert nagg1 == nagg + 2 and agg1[n] != agg1[n + 1]
+    assert np.sum(agg1[:n] == agg1[n]) == 0 and np.sum(agg1[:n] == agg1[n + 1]) == 0    # singletons
+    same = agg[:n, None] == agg[None, :n]
+    assert np.array_equal(same, agg1[:n, None] == agg1[None, :n])                       # same partition
+
+
+def test_chain_drops_isolated_rows_on_a_bar_only():
+    """eps = 1e-4 makes the collapsed columns of the coarse A_bar levels nearly diagonal (their
+    vertical coupling to the Dirichlet top dominates), so some of their nodes have no strong
+    coupling: those rows of P are empty on the A_bar chain; the singular surface chain keeps
+    every node."""
+    m = _mesh(48, 16, h0=1e-4, zj=0.3, seed=3)
+    P = O.Problem(m)
+    dropped = 0
+    for l in range(P.nlev(1) - 1):
+        agg = P.ints("lev.agg", 1, l)
+        Pm = P.csr("lev.P", 1, l)
+        rows = np.diff(Pm.indptr)
+        assert np.all(rows[agg < 0] == 0) and np.all(rows[agg >= 0] > 0)
+        dropped += int((agg < 0).sum())
+    assert dropped > 0
+    for l in range(P.nlev(0) - 1):
+        assert np.all(P.ints("lev.agg", 0, l) >= 0)
+
+
 def test_colouring_is_proper():
     m = _mesh(6, 4, zj=0.3)
     P = O.Problem(m)
