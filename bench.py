@@ -38,7 +38,7 @@ PRECONDS = {"additive": 0, "vl_sor": 1, "sa": 2}
 PRECS = {"fp64": 0, "fp32": 1, "bf16": 2}
 DTYPES = {"fp64": "f64", "fp32": "f64 outer + f32 preconditioner",
           "bf16": "f64 outer + f32 preconditioner with bf16 operator values"}
-SOR_FINE_DRAM_RATIO = 21.2 / 20.2   # ncu DRAM bytes / algorithmic bytes, finest FP32 colour sweep
+SOR_FINE_DRAM_RATIO = 34.63 / 32.33   # ncu DRAM bytes / algorithmic bytes, finest FP32 colour sweep
 CYCLES = {"persistent": 0, "launches": 1, "auto": 2, "hybrid": 3}
 
 
@@ -563,7 +563,8 @@ def main():
         dom = max((c for c in classes if c != "sor_all"), key=lambda c: classes[c]["ms_per_solve"])
         c = classes[dom]
         # DRAM traffic per launch of the finest-level FP32 colour sweep, from one ncu capture on a
-        # 192x192x32 mesh: 1.05 x its algorithmic bytes, scaled here by this workload's bytes per launch
+        # 192x192x32 mesh (colour 2, 261,577 rows): 1.07 x its algorithmic bytes, scaled here by
+        # this workload's bytes per launch
         traffic = None
         if dom == "sor_fine" and args.precision == "fp32":
             traffic = {"bytes_per_launch": SOR_FINE_DRAM_RATIO * c["bytes_per_launch"],
