@@ -331,23 +331,29 @@ __global__ void __launch_bounds__(kPThreads, 3) k_precond_persistent(const PPhas
 
 // The coarse tail of one chain (every level from a small one down, and back up) in one CTA: the
 // phases are separated by __syncthreads() instead of kernel boundaries. Launched on the stream of
-// the launch-per-phase cycle in place of the tail's dozens of small dependent launches. (A
-// thread-block cluster of 8 CTAs with the hardware cluster barrier, tried for larger tails, was
-// slower than the launches it replaced.)
-static constexpr int kTailThreads = 1024;
+// the launch-per-phase cycle in place of the tail's dozens of small dependent launches. Every
+// phase descriptor sits in shared memory, and each warp loads the operator data of its first row
+// of the next phase (slice metadata, first entries, diagonal: setup data) before the barrier, so
+// after it only the gathers of x remain; phase 0's is loaded before the wait on the previous
+// kernel. (A thread-block cluster of 8 CTAs with the hardware cluster barrier, tried for larger
+// tails, was slower than the launches it replaced.)
+static constexpr int kTailThreads = 512;
+static constexpr int kTailMaxPhases = 160;
 
 template <class XT>
 __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const PPhase *__restrict__ phases, int nphases) {
-    pdl_begin();
-    __shared__ PPhase sp;
+    __shared__ PPhase sp[kTailMaxPhases];
     const int gw = (int)(threadIdx.x >> 5), nw = kTailThreads / 32, lane = threadIdx.x & 31;
-    Pre<XT> none;
-    none.s = -1;
+    for (int q = threadIdx.x; q < nphases * kPhaseWords; q += kTailThreads)
+        ((int *)sp)[q] = __ldg((const int *)phases + q);
+    __syncthreads();
+    Pre<XT> pre;
+    prefetch<XT>(sp[0], nullptr, gw, lane, pre);
+    pdl_begin();
     for (int k = 0; k < nphases; ++k) {
-        if (threadIdx.x < kPhaseWords) ((int *)&sp)[threadIdx.x] = __ldg((const int *)(phases + k) + threadIdx.x);
-        __syncthreads();
-        run_phase<XT, false>(sp, nullptr, gw, nw, lane, none);
-        __syncthreads();   // the phase's writes are visible to the CTA; sp may be overwritten
+        run_phase<XT, true>(sp[k], nullptr, gw, nw, lane, pre);
+        if (k + 1 < nphases) prefetch<XT>(sp[k + 1], nullptr, gw, lane, pre);
+        __syncthreads();   // the phase's writes are visible to the CTA
     }
 }
 
@@ -610,7 +616,12 @@ static void build_tail(Arena &ar, SChain &C, bool fp32, int tail_rows, cudaStrea
     if (l0 < 0) return;
     Builder B(ar, s);
     B.xs = fp32 ? 4 : 8;
-    B.vcycle(C, l0, C.lv[l0].b, -1, C.lv[l0].x);
+    for (;;) {   // start deeper while the tail's phases do not fit in the kernel's shared memory
+        B.ph.clear();
+        B.vcycle(C, l0, C.lv[l0].b, -1, C.lv[l0].x);
+        if ((int)B.ph.size() <= kTailMaxPhases) break;
+        if (++l0 >= C.nlev) return;
+    }
     PPhase *d = ar.alloc<PPhase>((int)B.ph.size());
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
     VEMG_CHECK_CUDA(cudaMemcpy(d, B.ph.data(), sizeof(PPhase) * B.ph.size(), cudaMemcpyHostToDevice));

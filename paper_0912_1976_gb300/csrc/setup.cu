@@ -1128,74 +1128,112 @@ __global__ void k_offdiag_degree(int n, const int *__restrict__ rp, const int *_
     rank[i] = -1;
 }
 
-// the minimum remaining degree (dmin) and the number of remaining nodes (alive) of one round
-__global__ void k_sl_min(int n, const int *__restrict__ deg, const int *__restrict__ rank, int *dmin, int *alive) {
+// The rounds work on worklists: a round touches only the nodes it handles and their
+// neighbours, so that a round costs about one small kernel launch (the peeling needs thousands
+// of rounds on the finest levels).
+static constexpr int kRoundBlocks = 152, kRoundThreads = 256;
+static constexpr int kRing = 64;   // worklist sizes of the rounds, kept in a ring (> kRoundBatch + 2)
+
+__device__ __forceinline__ void push(int *wl, int *count, int v) { wl[atomicAdd(count, 1)] = v; }
+
+// Peeling round: every node of the worklist leaves with rank `round`; each remaining neighbour
+// loses one degree, and one whose degree falls from k + 1 to k joins the next worklist. (A
+// neighbour leaving in the same round has degree <= k already and never crosses.) One warp per
+// node, its lanes over the node's row, so that the decrements of a row are one round trip.
+// The worklist sizes live in a ring: round t reads slot t, fills slot t + 1 and clears slot
+// t + 2 for the round after it.
+__global__ void __launch_bounds__(kRoundThreads) k_peel_round(const int *__restrict__ wl_in, int *wl_out,
+                                                             int *nring, const int *__restrict__ rp,
+                                                             const int *__restrict__ ci, int *rank, int *deg, int k,
+                                                             int round, int *removed) {
+    const int cnt = nring[round % kRing];
+    int *n_out = nring + (round + 1) % kRing;
+    if (blockIdx.x == 0 && threadIdx.x == 0) nring[(round + 2) % kRing] = 0;
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int q = w0; q < cnt; q += nw) {
+        int v = wl_in[q];
+        if (lane == 0) rank[v] = round;
+        for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) {
+            int j = ci[e];
+            if (j != v && rank[j] < 0 && atomicSub(deg + j, 1) == k + 1) push(wl_out, n_out, j);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(removed, cnt);
+}
+
+// threshold raise: the smallest degree of the remaining nodes, then every remaining node of at
+// most that degree as the next worklist
+__global__ void k_peel_min(int n, const int *__restrict__ deg, const int *__restrict__ rank, int *dmin) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool in = i < n && rank[i] < 0;
     unsigned d = in ? (unsigned)deg[i] : 0xffffffffu;
     unsigned m = __reduce_min_sync(0xffffffffu, d);
-    unsigned c = __popc(__ballot_sync(0xffffffffu, in));
-    if ((threadIdx.x & 31) == 0 && c > 0) {
-        atomicMin(dmin, (int)m);
-        atomicAdd(alive, (int)c);
-    }
+    if ((threadIdx.x & 31) == 0 && m != 0xffffffffu) atomicMin(dmin, (int)m);
 }
 
-// kth[0] holds the previous round's threshold; the round's own goes to kth[1]
-__global__ void k_sl_take(int n, const int *__restrict__ deg, int *rank, const int *__restrict__ dmin, int *kth,
-                          int round) {
+__global__ void k_peel_fill(int n, const int *__restrict__ deg, const int *__restrict__ rank, int k, int *wl,
+                            int *count) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int k = max(kth[0], *dmin);
-    if (i == 0) kth[1] = k;
-    if (i < n && rank[i] < 0 && deg[i] <= k) rank[i] = round;
+    if (i < n && rank[i] < 0 && deg[i] <= k) push(wl, count, i);
 }
 
-__global__ void k_sl_update(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                            const int *__restrict__ rank, int *deg, int round) {
+// number of neighbours with a larger colouring key: a node is coloured once they all are
+__global__ void k_jp_pred(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                          const int *__restrict__ rank, int *pc, int *wl, int *count) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || rank[i] != round) return;
+    if (i >= n) return;
+    uint64_t ki = colour_key(rank[i], i);
+    int c = 0;
     for (int k = rp[i]; k < rp[i + 1]; ++k) {
         int j = ci[k];
-        if (j != i && rank[j] < 0) atomicSub(deg + j, 1);
+        c += j != i && colour_key(rank[j], j) > ki;
     }
+    pc[i] = c;
+    if (c == 0) push(wl, count, i);
 }
 
-__global__ void k_jp_winners(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                             const int *__restrict__ rank, const int *__restrict__ colour, int *win, int *left) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool unc = i < n && colour[i] < 0;
-    unsigned c = __popc(__ballot_sync(0xffffffffu, unc));
-    if ((threadIdx.x & 31) == 0 && c > 0) atomicAdd(left, (int)c);
-    if (i >= n) return;
-    int w = 0;
-    if (unc) {
-        uint64_t ki = colour_key(rank[i], i);
-        w = 1;
-        for (int k = rp[i]; k < rp[i + 1] && w; ++k) {
-            int j = ci[k];
-            if (j == i || colour[j] >= 0) continue;
-            if (colour_key(rank[j], j) > ki) w = 0;
+// Jones-Plassmann round: every node of the worklist (all its larger-key neighbours coloured; no
+// two of them neighbours, since the smaller-key one would still wait for the other) takes the
+// smallest colour none of its coloured neighbours has, then releases its smaller-key
+// neighbours; one released by its last larger-key neighbour joins the next worklist. One warp
+// per node: its lanes read the row's colours into a bit mask (colours below 64; a row that uses
+// all 64 scans on), then decrement the counts.
+__global__ void __launch_bounds__(kRoundThreads) k_jp_round(const int *__restrict__ wl_in, int *wl_out, int *nring,
+                                                           int round, const int *__restrict__ rp,
+                                                           const int *__restrict__ ci, const int *__restrict__ rank,
+                                                           int *pc, int *colour, int *maxc) {
+    const int cnt = nring[round % kRing];
+    int *n_out = nring + (round + 1) % kRing;
+    if (blockIdx.x == 0 && threadIdx.x == 0) nring[(round + 2) % kRing] = 0;
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int q = w0; q < cnt; q += nw) {
+        const int v = wl_in[q];
+        const int lo = rp[v], hi = rp[v + 1];
+        int col = -1;
+        for (int base = 0; col < 0; base += 64) {
+            unsigned long long used = 0ull;
+            for (int e = lo + lane; e < hi; e += 32) {
+                int j = ci[e];
+                int c = j != v ? colour[j] - base : -1;
+                if (c >= 0 && c < 64) used |= 1ull << c;
+            }
+            unsigned lo32 = __reduce_or_sync(0xffffffffu, (unsigned)used);
+            unsigned hi32 = __reduce_or_sync(0xffffffffu, (unsigned)(used >> 32));
+            unsigned long long all = ((unsigned long long)hi32 << 32) | lo32;
+            if (all != ~0ull) col = base + __ffsll((long long)~all) - 1;
+        }
+        if (lane == 0) {
+            colour[v] = col;
+            atomicMax(maxc, col);
+        }
+        const uint64_t kv = colour_key(rank[v], v);
+        for (int e = lo + lane; e < hi; e += 32) {
+            int j = ci[e];
+            if (j != v && colour_key(rank[j], j) < kv && atomicSub(pc + j, 1) == 1) push(wl_out, n_out, j);
         }
     }
-    win[i] = w;
-}
-
-__global__ void k_jp_assign(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                            const int *__restrict__ win, int *colour, int *maxc) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || !win[i]) return;
-    int c = 0;
-    for (;;) {
-        bool used = false;
-        for (int k = rp[i]; k < rp[i + 1] && !used; ++k) {
-            int j = ci[k];
-            if (j != i && colour[j] == c) used = true;
-        }
-        if (!used) break;
-        ++c;
-    }
-    colour[i] = c;
-    atomicMax(maxc, c);
 }
 
 __global__ void k_eq_flag(int n, const int *__restrict__ key, int c, int *flag) {
@@ -1213,37 +1251,45 @@ static void colour_level(Arena &ar, Level &L, cudaStream_t s) {
     int n = L.A.n;
     L.colour = ar.alloc<int>(n);
     VEMG_CHECK_CUDA(cudaMemsetAsync(L.colour, 0xff, sizeof(int) * n, s));
-    // per-round slots: every round removes at least one node, so there are at most n rounds
-    // (plus the rounds of the last batch launched after the peeling ended, which do nothing)
-    const int64_t slots = (int64_t)n + kRoundBatch + 2;
-    Scratch<int> deg(n), rank(n), win(n), maxc(1), dmin(slots), kth(slots), cnt(slots);
+    Scratch<int> deg(n), rank(n), pc(n), wl0(n), wl1(n), maxc(1), nring(kRing), removed(1), dmin(1);
+    int *wl[2] = {wl0, wl1};
+    VEMG_CHECK_CUDA(cudaMemsetAsync(maxc, 0, sizeof(int), s));
     if (n > 0) {
         k_offdiag_degree<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, deg, rank);
         VEMG_CHECK_LAUNCH();
-        VEMG_CHECK_CUDA(cudaMemsetAsync(dmin, 0x7f, sizeof(int) * slots, s));   // 0x7f7f7f7f: no node
-        VEMG_CHECK_CUDA(cudaMemsetAsync(kth, 0, sizeof(int) * slots, s));
-        VEMG_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * slots, s));
+        VEMG_CHECK_CUDA(cudaMemsetAsync(nring, 0, sizeof(int) * kRing, s));
+        VEMG_CHECK_CUDA(cudaMemsetAsync(removed, 0, sizeof(int), s));
     }
-    // peeling, kRoundBatch rounds per host check
-    for (int r0 = 0; n > 0; r0 += kRoundBatch) {
-        for (int t = r0; t < r0 + kRoundBatch; ++t) {
-            k_sl_min<<<grid_for(n, 256), 256, 0, s>>>(n, deg, rank, dmin + t, cnt + t);
-            k_sl_take<<<grid_for(n, 256), 256, 0, s>>>(n, deg, rank, dmin + t, kth + t, t);
-            k_sl_update<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, rank, deg, t);
+    // peeling: raise the threshold whenever the worklist runs empty, else kRoundBatch rounds per
+    // host check (rounds after an empty worklist do nothing; their ranks stay unused, which
+    // keeps the order of the ranks)
+    int t = 0, k = 0;
+    while (n > 0 && read_int(removed, s) < n) {
+        if (read_int(nring + t % kRing, s) == 0) {
+            VEMG_CHECK_CUDA(cudaMemsetAsync(dmin, 0x7f, sizeof(int), s));
+            k_peel_min<<<grid_for(n, 256), 256, 0, s>>>(n, deg, rank, dmin);
+            VEMG_CHECK_LAUNCH();
+            k = std::max(k, read_int(dmin, s));
+            k_peel_fill<<<grid_for(n, 256), 256, 0, s>>>(n, deg, rank, k, wl[t & 1], nring + t % kRing);
             VEMG_CHECK_LAUNCH();
         }
-        // nodes present at the start of the batch's last round: none means the peeling is done
-        if (read_int(cnt + (r0 + kRoundBatch - 1), s) == 0) break;
+        for (int u = 0; u < kRoundBatch; ++u, ++t)
+            k_peel_round<<<kRoundBlocks, kRoundThreads, 0, s>>>(wl[t & 1], wl[(t + 1) & 1], nring, L.A.rp, L.A.ci,
+                                                                rank, deg, k, t, removed);
+        VEMG_CHECK_LAUNCH();
     }
-    VEMG_CHECK_CUDA(cudaMemsetAsync(maxc, 0, sizeof(int), s));
-    for (int batch = 0; n > 0; ++batch) {
-        VEMG_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * kRoundBatch, s));
-        for (int t = 0; t < kRoundBatch; ++t) {
-            k_jp_winners<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, rank, L.colour, win, cnt + t);
-            k_jp_assign<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, win, L.colour, maxc);
-            VEMG_CHECK_LAUNCH();
-        }
-        if (read_int(cnt + (kRoundBatch - 1), s) == 0) break;
+    // colouring in decreasing key order: Jones-Plassmann rounds on predecessor counts
+    if (n > 0) {
+        VEMG_CHECK_CUDA(cudaMemsetAsync(nring, 0, sizeof(int) * kRing, s));
+        k_jp_pred<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, rank, pc, wl[0], nring);
+        VEMG_CHECK_LAUNCH();
+    }
+    for (t = 0; n > 0;) {
+        for (int u = 0; u < kRoundBatch; ++u, ++t)
+            k_jp_round<<<kRoundBlocks, kRoundThreads, 0, s>>>(wl[t & 1], wl[(t + 1) & 1], nring, t, L.A.rp, L.A.ci,
+                                                              rank, pc, L.colour, maxc);
+        VEMG_CHECK_LAUNCH();
+        if (read_int(nring + t % kRing, s) == 0) break;   // every node coloured
     }
     L.ncolours = n > 0 ? read_int(maxc, s) + 1 : 0;
     L.crow = ar.alloc<int>(n);
