@@ -107,6 +107,7 @@ static double *gsc(BatchWork *w) { return w->sc + B_COUNT * w->K; }
 enum { BOP_SPMV = 0, BOP_SPMV_ADD = 1, BOP_SOR = 2, BOP_RES = 3 };
 
 __global__ void k_bto_float(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+    pdl_begin();
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
 }
@@ -121,7 +122,10 @@ __global__ void __launch_bounds__(32 * kSellWarps) k_bcsr(int nrows, const int *
                                                          int cur) {
     constexpr int RW = 32 / KW;
     int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (w * RW >= nrows) return;   // warp-uniform
+    if (w * RW >= nrows) {   // warp-uniform
+        pdl_begin();
+        return;
+    }
     int idx = w * RW + lane / KW;
     bool valid = idx < nrows;
     int r = valid ? (rows ? rows[idx] : r0 + idx) : 0;
@@ -130,14 +134,27 @@ __global__ void __launch_bounds__(32 * kSellWarps) k_bcsr(int nrows, const int *
     const int gl = lane % KW, gb = lane - gl;
     const bool skip_all = OP == BOP_SOR && cur == 0;
     int wmax = __reduce_max_sync(0xffffffffu, (unsigned)wd);
+    // the row's first KW entries are setup data: loaded before waiting on the previous kernel
+    int cc0 = -1;
+    VT vv0 = (VT)0;
+    if (!skip_all) {
+        cc0 = gl < wd ? __ldg(A.ci + lo + gl) : -1;
+        vv0 = gl < wd ? __ldg(v + lo + gl) : (VT)0;
+        if (OP == BOP_SOR && cc0 >= 0 && (cc0 == r || (cur > 0 && __ldg(colour + cc0) >= cur))) cc0 = -1;
+    }
+    pdl_begin();
     for (int c = gl; c < K; c += KW) {
         AT acc = 0;
         if (!skip_all) {
             for (int k0 = 0; k0 < wmax; k0 += KW) {
                 int k = k0 + gl;
-                int cc = k < wd ? __ldg(A.ci + lo + k) : -1;
-                VT vv = k < wd ? __ldg(v + lo + k) : (VT)0;
-                if (OP == BOP_SOR && cc >= 0 && (cc == r || (cur > 0 && __ldg(colour + cc) >= cur))) cc = -1;
+                int cc = cc0;
+                VT vv = vv0;
+                if (k0 > 0) {
+                    cc = k < wd ? __ldg(A.ci + lo + k) : -1;
+                    vv = k < wd ? __ldg(v + lo + k) : (VT)0;
+                    if (OP == BOP_SOR && cc >= 0 && (cc == r || (cur > 0 && __ldg(colour + cc) >= cur))) cc = -1;
+                }
                 int nj = min(KW, wmax - k0);
 #pragma unroll
                 for (int jj = 0; jj < KW; ++jj) {
@@ -166,10 +183,14 @@ __global__ void __launch_bounds__(32 * kSellWarps) k_bcsr_narrow(int nrows, cons
                                                                 const int *__restrict__ colour, int cur) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int idx = (int)(t / KW), c = (int)(t % KW);
-    if (idx >= nrows) return;
+    if (idx >= nrows) {
+        pdl_begin();
+        return;
+    }
     int r = rows ? rows[idx] : r0 + idx;
     int lo = A.rp[r], hi = A.rp[r + 1];
     const VT *v = (const VT *)A.v;
+    pdl_begin();
     AT acc = 0;
     if (!(OP == BOP_SOR && cur == 0)) {
         for (int k0 = lo; k0 < hi; k0 += kBU) {
@@ -203,9 +224,9 @@ static void bcsr(CsrP A, int nrows, const int *rows, int r0, const VT *dg, const
     if (KW < 4) {
         int64_t t = (int64_t)nrows * KW;
         if (KW == 1)
-            k_bcsr_narrow<OP, VT, XT, BT, YT, AT, 1><<<grid_for(t, 32 * kSellWarps), blk, 0, s>>>(nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+            pdl_launch(k_bcsr_narrow<OP, VT, XT, BT, YT, AT, 1>, grid_for(t, 32 * kSellWarps), blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
         else
-            k_bcsr_narrow<OP, VT, XT, BT, YT, AT, 2><<<grid_for(t, 32 * kSellWarps), blk, 0, s>>>(nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+            pdl_launch(k_bcsr_narrow<OP, VT, XT, BT, YT, AT, 2>, grid_for(t, 32 * kSellWarps), blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
         BATCH_LAUNCHED();
         return;
     }
@@ -213,10 +234,10 @@ static void bcsr(CsrP A, int nrows, const int *rows, int r0, const VT *dg, const
     int64_t warps = (nrows + RW - 1) / RW;
     int grid = (int)((warps + kSellWarps - 1) / kSellWarps);
     switch (KW) {
-        case 4: k_bcsr<OP, VT, XT, BT, YT, AT, 4><<<grid, blk, 0, s>>>(nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
-        case 8: k_bcsr<OP, VT, XT, BT, YT, AT, 8><<<grid, blk, 0, s>>>(nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
-        case 16: k_bcsr<OP, VT, XT, BT, YT, AT, 16><<<grid, blk, 0, s>>>(nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
-        default: k_bcsr<OP, VT, XT, BT, YT, AT, 32><<<grid, blk, 0, s>>>(nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
+        case 4: pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 4>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
+        case 8: pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 8>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
+        case 16: pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 16>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
+        default: pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 32>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
     }
     BATCH_LAUNCHED();
 }
@@ -224,6 +245,7 @@ static void bcsr(CsrP A, int nrows, const int *rows, int r0, const VT *dg, const
 // x = G b on the coarsest level, one thread per (row, column)
 template <class XT, class BT>
 __global__ void k_bdense(int n, const XT *__restrict__ G, const BT *__restrict__ b, XT *__restrict__ x, int K) {
+    pdl_begin();
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)n * K) return;
     int r = (int)(t >> (__ffs(K) - 1)), c = (int)(t & (K - 1));
@@ -251,7 +273,7 @@ static void bvcycle(const BChain &C, BatchWork *W, int ch, int l, const BT *b, X
         if (C.direct) {
             int64_t t = (int64_t)C.nc * K;
             const XT *G = sizeof(XT) == sizeof(float) ? (const XT *)C.Gf : (const XT *)C.G;
-            k_bdense<XT, BT><<<grid_for(t, 256), 256, 0, s>>>(C.nc, G, b, x, K);
+            pdl_launch(k_bdense<XT, BT>, grid_for(t, 256), 256, s, C.nc, G, b, x, K);
             BATCH_LAUNCHED();
             return;
         }
@@ -310,6 +332,7 @@ struct BSums {
 
 template <int NS>
 __global__ void __launch_bounds__(kBT) k_bsums(int64_t N, int K, BSums d, double *part) {
+    pdl_begin();
     double acc[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) acc[s] = 0.0;
@@ -338,6 +361,7 @@ template <int NS>
 __global__ void __launch_bounds__(kBT, 2) k_bsums_zrq(int64_t N, int K, const double *__restrict__ z,
                                                       const double *__restrict__ r, const double *__restrict__ q,
                                                       double *part) {
+    pdl_begin();
     double acc[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) acc[s] = 0.0;
@@ -488,6 +512,7 @@ __global__ void k_bprepare(int64_t N, int K, int neumann, double *__restrict__ b
 // X += alpha P, R -= alpha Q per column
 __global__ void k_bupdate_xr(int64_t N, int K, const double *__restrict__ p, const double *__restrict__ q,
                              double *__restrict__ x, double *__restrict__ r, const double *__restrict__ sc) {
+    pdl_begin();
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= N) return;
     double a = sc[B_ALPHA * K + (int)(e & (K - 1))];
@@ -498,6 +523,7 @@ __global__ void k_bupdate_xr(int64_t N, int K, const double *__restrict__ p, con
 // z += x (assign: z = x)
 template <class XT>
 __global__ void k_badd(int64_t N, const XT *__restrict__ x, double *__restrict__ z, int assign = 0) {
+    pdl_begin();
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= N) return;
     z[e] = assign ? (double)x[e] : z[e] + (double)x[e];
@@ -506,6 +532,7 @@ __global__ void k_badd(int64_t N, const XT *__restrict__ x, double *__restrict__
 // P = (Z - mu) + beta P per column
 __global__ void k_bupdate_p(int64_t N, int K, const double *__restrict__ sc, const double *__restrict__ z,
                             double *__restrict__ p) {
+    pdl_begin();
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= N) return;
     int c = (int)(e & (K - 1));
@@ -575,7 +602,7 @@ static void bprecond(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_join, h->side));
         const int64_t nbk = (int64_t)(h->n - mt) * K;
         if (std::is_same<XT, float>::value && W->Rb32) {
-            k_bto_float<<<grid_for(nbk, 256), 256, 0, s>>>(nbk, W->R + (int64_t)mt * K, W->Rb32);
+            pdl_launch(k_bto_float, grid_for(nbk, 256), 256, s, nbk, (const double *)(W->R + (int64_t)mt * K), W->Rb32);
             BATCH_LAUNCHED();
             bvcycle<XT, XT>(*W->bbar, W, 1, 0, (const XT *)W->Rb32, xb, s);
         } else {
@@ -591,12 +618,12 @@ static void bprecond(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
             bcsr<BOP_SPMV, double, XT, double, double, double>(CsrP{h->E.rp, h->E.ci, h->E.v}, h->n, nullptr, 0,
                                                                (const double *)nullptr, (const double *)nullptr, x0,
                                                                W->Z, K, nullptr, -1, s);
-        k_badd<XT><<<grid_for(nbk, 256), 256, 0, s>>>(nbk, xb, W->Z + (int64_t)mt * K);
+        pdl_launch(k_badd<XT>, grid_for(nbk, 256), 256, s, nbk, (const XT *)xb, W->Z + (int64_t)mt * K, 0);
         BATCH_LAUNCHED();
     } else {
         bvcycle<XT, double>(*W->bbar, W, 1, 0, W->R, xb, s);
         int64_t N = (int64_t)h->nu * K;
-        k_badd<XT><<<grid_for(N, 256), 256, 0, s>>>(N, xb, W->Z, 1);
+        pdl_launch(k_badd<XT>, grid_for(N, 256), 256, s, N, (const XT *)xb, W->Z, 1);
         BATCH_LAUNCHED();
     }
 }
@@ -604,9 +631,9 @@ static void bprecond(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
 static void bsums(BatchWork *W, int64_t N, const BSums &d, cudaStream_t s) {
     int nblk = stage1_blocks(N);
     switch (d.ns) {
-        case 1: k_bsums<1><<<nblk, kBT, 0, s>>>(N, W->K, d, W->part); break;
-        case 3: k_bsums<3><<<nblk, kBT, 0, s>>>(N, W->K, d, W->part); break;
-        default: k_bsums<5><<<nblk, kBT, 0, s>>>(N, W->K, d, W->part); break;
+        case 1: pdl_launch(k_bsums<1>, nblk, kBT, s, N, W->K, d, W->part); break;
+        case 3: pdl_launch(k_bsums<3>, nblk, kBT, s, N, W->K, d, W->part); break;
+        default: pdl_launch(k_bsums<5>, nblk, kBT, s, N, W->K, d, W->part); break;
     }
     BATCH_LAUNCHED();
 }
@@ -628,9 +655,11 @@ static void bprecond_any(vemg_hierarchy *h, BatchWork *W, int first, cudaStream_
     (void)first;
     const int ns = flex ? 5 : 3;
     if (flex)
-        k_bsums_zrq<5><<<stage1_blocks(N), kBT, 0, s>>>(N, W->K, W->Z, W->R, W->Q, W->part);
+        pdl_launch(k_bsums_zrq<5>, stage1_blocks(N), kBT, s, N, W->K, (const double *)W->Z, (const double *)W->R,
+                   (const double *)W->Q, W->part);
     else
-        k_bsums_zrq<3><<<stage1_blocks(N), kBT, 0, s>>>(N, W->K, W->Z, W->R, nullptr, W->part);
+        pdl_launch(k_bsums_zrq<3>, stage1_blocks(N), kBT, s, N, W->K, (const double *)W->Z, (const double *)W->R,
+                   (const double *)nullptr, W->part);
     BATCH_LAUNCHED();
     bstage2(h, W, ST_BETA, ns, N, first, s);
 }
@@ -663,7 +692,8 @@ static void bphase_step(vemg_hierarchy *h, BatchWork *W, cudaStream_t s, cudaGra
         bsums(W, N, d, s);
         bstage2(h, W, ST_ALPHA, 1, N, 0, s);
     }
-    k_bupdate_xr<<<grid_for(N, 256), 256, 0, s>>>(N, K, W->P, W->Q, W->X, W->R, W->sc);
+    pdl_launch(k_bupdate_xr, grid_for(N, 256), 256, s, N, K, (const double *)W->P, (const double *)W->Q, W->X, W->R,
+               (const double *)W->sc);
     BATCH_LAUNCHED();
     {
         BSums d{{W->R}, {W->R}, 1};
@@ -675,7 +705,7 @@ static void bphase_step(vemg_hierarchy *h, BatchWork *W, cudaStream_t s, cudaGra
 static void bphase_direction(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
     bprecond_any(h, W, 0, s);
     int64_t N = (int64_t)h->nu * W->K;
-    k_bupdate_p<<<grid_for(N, 256), 256, 0, s>>>(N, W->K, W->sc, W->Z, W->P);
+    pdl_launch(k_bupdate_p, grid_for(N, 256), 256, s, N, W->K, (const double *)W->sc, (const double *)W->Z, W->P);
     BATCH_LAUNCHED();
 }
 
