@@ -168,28 +168,35 @@ __device__ __forceinline__ AT sell_row(const int *__restrict__ col, const VT *__
     return sell_row<VT, XT, AT>(h, col, v, o, w, x, lim);
 }
 
-// y = A x (add: y += A x) over the slices [s0, s1); accumulation in AT
+// y = A x (add: y += A x) over the slices [s0, s1); accumulation in AT. With x0: the restriction
+// into a level whose V-cycle starts with a sweep from x = 0 also does that sweep's first colour
+// (rows below lim0): x0_i = y_i / A_ii, the same product the colour's own launch would form.
 template <class VT, class XT, class YT, class AT>
 __global__ void __launch_bounds__(kSellBlock) k_sell_spmv(int s0, int s1, const int *__restrict__ row0,
                                                           const int *__restrict__ nrow, const int *__restrict__ off,
                                                           const int *__restrict__ width, const int *__restrict__ col,
                                                           const VT *__restrict__ v, const XT *__restrict__ x,
-                                                          YT *__restrict__ y, int add) {
+                                                          YT *__restrict__ y, int add, const YT *__restrict__ dinv0,
+                                                          YT *__restrict__ x0, int lim0) {
     int s = s0 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     const bool active = s < s1 && lane < nrow[s];
     RowHead<VT> h;
     int o = 0, w = 0, r = 0;
+    YT d0 = 0;
     if (active) {
         o = off[s] + lane;
         w = width[s];
         r = row0[s] + lane;
+        if (x0 && r < lim0) d0 = dinv0[r];
         load_head(h, col, v, o, w);
     }
     pdl_begin();
     if (!active) return;
     AT acc = sell_row<VT, XT, AT>(h, col, v, o, w, x, -1);
-    y[r] = add ? (YT)((AT)y[r] + acc) : (YT)acc;
+    YT yr = add ? (YT)((AT)y[r] + acc) : (YT)acc;
+    y[r] = yr;
+    if (x0 && r < lim0) x0[r] = yr * d0;
 }
 
 // SOR (omega = 1) on the rows of one colour (slices [s0, s1)):
@@ -265,15 +272,20 @@ __global__ void k_dense_mv(int n, const XT *__restrict__ Gm, const BT *__restric
 // launch wrappers
 
 template <class VT, class XT, class YT, class AT>
-static void sell_spmv(const Sell &S, const XT *x, YT *y, int add, cudaStream_t s) {
+static void sell_spmv(const Sell &S, const XT *x, YT *y, int add, cudaStream_t s, const SLevel *first = nullptr) {
     if (S.nslices == 0) return;
     int64_t threads = (int64_t)S.nslices * 32;
+    // first: the level y feeds, whose from-zero sweep's first colour this launch also does
+    const YT *d0 = first ? (const YT *)first->dinv : nullptr;
+    YT *x0 = first ? (YT *)first->x : nullptr;
+    const int lim0 = first ? first->crow[1] : 0;
     if (S.vh)   // BF16 values (FP32 vectors)
         pdl_launch(k_sell_spmv<__nv_bfloat16, XT, YT, AT>, grid_for(threads, kSellBlock), kSellBlock, s, 0,
-                   S.nslices, S.row0, S.nrow, S.off, S.width, S.col, (const __nv_bfloat16 *)S.vh, x, y, add);
+                   S.nslices, S.row0, S.nrow, S.off, S.width, S.col, (const __nv_bfloat16 *)S.vh, x, y, add, d0, x0,
+                   lim0);
     else
         pdl_launch(k_sell_spmv<VT, XT, YT, AT>, grid_for(threads, kSellBlock), kSellBlock, s, 0, S.nslices,
-                   S.row0, S.nrow, S.off, S.width, S.col, (const VT *)S.v, x, y, add);
+                   S.row0, S.nrow, S.off, S.width, S.col, (const VT *)S.v, x, y, add, d0, x0, lim0);
     SOLVE_LAUNCHED();
 }
 
@@ -283,9 +295,11 @@ static double value_bytes(const Sell &S) {
     return S.vh ? 2.0 : (double)sizeof(XT);
 }
 
+// skip0: a from-zero sweep whose first colour the restriction into this level already did
 template <class XT, class BT>
-static void sor_sweep(const SLevel &L, const BT *b, XT *x, bool forward, bool from_zero, bool fine, cudaStream_t s) {
-    for (int cc = 0; cc < L.ncolours; ++cc) {
+static void sor_sweep(const SLevel &L, const BT *b, XT *x, bool forward, bool from_zero, bool fine, cudaStream_t s,
+                      bool skip0 = false) {
+    for (int cc = skip0 ? 1 : 0; cc < L.ncolours; ++cc) {
         int c = forward ? cc : L.ncolours - 1 - cc;
         int s0 = L.cslice[c], s1 = L.cslice[c + 1];
         if (s1 == s0) continue;
@@ -322,9 +336,18 @@ static void residual(const SLevel &L, const BT *b, const XT *x, XT *r, cudaStrea
     SOLVE_LAUNCHED();
 }
 
-// V-cycle with a zero initial guess (section 5.1); b of level 0 may be FP64 (the outer residual)
+// whether the restriction into level l does the first colour of its from-zero sweep (levels
+// swept one kernel per colour: not the dense coarsest level, not a single-CTA tail)
+static bool fused_first(const SChain &C, int l) {
+    if (l >= C.nlev || C.lv[l].ncolours < 1) return false;
+    if (l == C.nlev - 1 && C.direct) return false;
+    return !(l > 0 && l == C.tail_level);
+}
+
+// V-cycle with a zero initial guess (section 5.1); b of level 0 may be FP64 (the outer residual).
+// first_done: the first colour of the pre-smoothing sweep was done by the restriction into l.
 template <class XT, class BT>
-static void vcycle_level(const SChain &C, int l, const BT *b, XT *x, cudaStream_t s) {
+static void vcycle_level(const SChain &C, int l, const BT *b, XT *x, cudaStream_t s, bool first_done = false) {
     const SLevel &L = C.lv[l];
     const bool fine = C.is_bar && l == 0;
     if (l > 0 && l == C.tail_level) {
@@ -342,15 +365,16 @@ static void vcycle_level(const SChain &C, int l, const BT *b, XT *x, cudaStream_
             return;
         }
         // coarsening stalled above the direct-solve size: one symmetric SOR pass
-        sor_sweep<XT, BT>(L, b, x, true, true, fine, s);
+        sor_sweep<XT, BT>(L, b, x, true, true, fine, s, first_done);
         sor_sweep<XT, BT>(L, b, x, false, false, fine, s);
         return;
     }
-    sor_sweep<XT, BT>(L, b, x, true, true, fine, s);
+    sor_sweep<XT, BT>(L, b, x, true, true, fine, s, first_done);
     residual<XT, BT>(L, b, x, (XT *)L.r, s);
     const SLevel &N = C.lv[l + 1];
-    sell_spmv<XT, XT, XT, XT>(L.PT, (const XT *)L.r, (XT *)N.b, 0, s);
-    vcycle_level<XT, XT>(C, l + 1, (const XT *)N.b, (XT *)N.x, s);
+    const bool fuse = fused_first(C, l + 1);
+    sell_spmv<XT, XT, XT, XT>(L.PT, (const XT *)L.r, (XT *)N.b, 0, s, fuse ? &N : nullptr);
+    vcycle_level<XT, XT>(C, l + 1, (const XT *)N.b, (XT *)N.x, s, fuse);
     sell_spmv<XT, XT, XT, XT>(L.P, (const XT *)N.x, x, 1, s);
     sor_sweep<XT, BT>(L, b, x, false, false, fine, s);
 }
@@ -765,8 +789,9 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_fork, s));
         VEMG_CHECK_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         // surface branch: r_c = E~^T r accumulated in FP64, one V-cycle on E~^T A E~
-        sell_spmv<double, double, XT, double>(h->ETs, r, (XT *)S.lv[0].b, 0, h->side);
-        vcycle_level<XT, XT>(S, 0, (const XT *)S.lv[0].b, (XT *)S.lv[0].x, h->side);
+        const bool fuse = fused_first(S, 0);
+        sell_spmv<double, double, XT, double>(h->ETs, r, (XT *)S.lv[0].b, 0, h->side, fuse ? &S.lv[0] : nullptr);
+        vcycle_level<XT, XT>(S, 0, (const XT *)S.lv[0].b, (XT *)S.lv[0].x, h->side, fuse);
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_join, h->side));
         ys = (const XT *)S.lv[0].x;
     }
