@@ -38,7 +38,9 @@ PRECONDS = {"additive": 0, "vl_sor": 1, "sa": 2}
 PRECS = {"fp64": 0, "fp32": 1, "bf16": 2}
 DTYPES = {"fp64": "f64", "fp32": "f64 outer + f32 preconditioner",
           "bf16": "f64 outer + f32 preconditioner with bf16 operator values"}
-SOR_FINE_DRAM_RATIO = 34.63 / 32.33   # ncu DRAM bytes / algorithmic bytes, finest FP32 colour sweep
+# ncu DRAM bytes / algorithmic bytes of the finest colour sweep (one launch, 192x192x32 mesh)
+SOR_FINE_DRAM_RATIO = {"fp32": 34.63 / 32.33, "bf16": 27.33 / 25.18}
+SOR_FINE_KERNEL = {"fp32": "k_sell_sor<float, float, double>", "bf16": "k_sell_sor<__nv_bfloat16, float, double>"}
 CYCLES = {"persistent": 0, "launches": 1, "auto": 2, "hybrid": 3}
 
 
@@ -48,7 +50,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vemg", choices=["vemg", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=list(PRECS))
+    ap.add_argument("--precision", default="bf16", choices=list(PRECS))
     ap.add_argument("--cycle", default="auto", choices=["auto", "persistent", "launches", "hybrid"],
                     help="one cooperative kernel per preconditioner application, one kernel per phase, or the "
                          "library's choice by precision")
@@ -535,7 +537,7 @@ def main():
         B = [torch.from_numpy(I.normal_loads(n, 4000 + 997 * rank + 131 * j, k=kr)).cuda() for j in range(nb)]
 
     res = {}
-    order = [args.precision] + [p for p in ("fp32", "fp64") if p != args.precision]
+    order = [args.precision] + [p for p in ("fp32", "fp64") if p != args.precision]   # comparators
     for prec in order:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -562,14 +564,14 @@ def main():
     if classes:
         dom = max((c for c in classes if c != "sor_all"), key=lambda c: classes[c]["ms_per_solve"])
         c = classes[dom]
-        # DRAM traffic per launch of the finest-level FP32 colour sweep, from one ncu capture on a
-        # 192x192x32 mesh (colour 2, 261,577 rows): 1.07 x its algorithmic bytes, scaled here by
-        # this workload's bytes per launch
+        # DRAM traffic per launch of the finest-level colour sweep, from one ncu capture on a
+        # 192x192x32 mesh (colour 2, 261,577 rows): 1.07 (FP32 values) / 1.09 (BF16 values) x its
+        # algorithmic bytes, scaled here by this workload's bytes per launch
         traffic = None
-        if dom == "sor_fine" and args.precision == "fp32":
-            traffic = {"bytes_per_launch": SOR_FINE_DRAM_RATIO * c["bytes_per_launch"],
-                       "source": "ncu dram__bytes (read + write) of one k_sell_sor<float, float, double> launch on a "
-                                 "192x192x32 mesh, scaled by algorithmic bytes per launch"}
+        if dom == "sor_fine" and args.precision in SOR_FINE_DRAM_RATIO:
+            traffic = {"bytes_per_launch": SOR_FINE_DRAM_RATIO[args.precision] * c["bytes_per_launch"],
+                       "source": f"ncu dram__bytes (read + write) of one {SOR_FINE_KERNEL[args.precision]} launch "
+                                 "on a 192x192x32 mesh, scaled by algorithmic bytes per launch"}
         roofline = {"bound": "hbm", "kernel": dom, "achieved": c["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                     "frac": c["achieved_gbs"] / hbm, "peak_source": f"{peak_kind} hbm_gbs (copy, burst)",
                     "traffic": traffic, "classes": classes}
@@ -590,6 +592,12 @@ def main():
                           "iters": f["iters"][0], "ms_per_step": f["ms_per_step"],
                           "e2e": f["e2e"]["value"], "true_relres_max": f["true_relres_max"],
                           "cycle": f["cycle"], "speedup_of_value": head["value"] / f["value"]}
+        fp32_line = None
+        if "fp32" in res and args.precision == "bf16":
+            f = res["fp32"]
+            fp32_line = {"name": "FP64 FCG with FP32 V-cycles and FP32 operator values", "value": f["value"],
+                         "iters": f["iters"][0], "ms_per_step": f["ms_per_step"], "e2e": f["e2e"]["value"],
+                         "true_relres_max": f["true_relres_max"]}
         line = {"metric": METRIC, "value": head["value"], "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
@@ -599,7 +607,7 @@ def main():
                 "true_relres_max": head["true_relres_max"], "setup_s": head["setup_s"],
                 "hierarchy_bytes": head["hierarchy_bytes"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": head["clocks"],
-                "plain_fp64_pcg": comparator}
+                "plain_fp64_pcg": comparator, "fp32_values": fp32_line}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
