@@ -86,7 +86,8 @@ def test_sampled_extrapolation_rows():
 @pytest.mark.parametrize("precision,cycle", [(V.VEMG_PREC_FP32, V.VEMG_CYCLE_AUTO),
                                              (V.VEMG_PREC_FP64, V.VEMG_CYCLE_AUTO),
                                              (V.VEMG_PREC_FP64, V.VEMG_CYCLE_PERSISTENT),
-                                             (V.VEMG_PREC_FP32, V.VEMG_CYCLE_HYBRID)])
+                                             (V.VEMG_PREC_FP32, V.VEMG_CYCLE_HYBRID),
+                                             (V.VEMG_PREC_BF16, V.VEMG_CYCLE_AUTO)])
 def test_full_size_solve_properties(precision, cycle):
     m, vm, A = _full()
     h = V.vemg_setup(A, vm, V.vemg_default_options(precision=precision, cycle=cycle))
