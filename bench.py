@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--serve", type=int, default=0,
                     help="serving workload: this many Poisson-arrival requests (512 for the full stream)")
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (0: 0.8 x saturation)")
+    ap.add_argument("--slots", type=int, default=8, help="serving: right-hand-side slots per engine")
     ap.add_argument("--case", default="",
                     help="profiling case NXxNYxNZ (z-jitter 0.3, eps 1e-3): two untimed solves, then exit")
     ap.add_argument("--spectrum", action="store_true",
@@ -351,7 +352,7 @@ def run_serve(args):
     from paper_0912_1976_gb300 import serve as S
     from paper_0912_1976_gb300 import vemg as V
     prec = PRECS[args.precision]
-    fac = S.GpuFactory(slots=8, precision=prec)
+    fac = S.GpuFactory(slots=args.slots, precision=prec)
     for i in range(len(S.SIZES)):                  # meshes are inputs: generated before the clock
         fac.mesh(i, 1.0)
     out = {}
@@ -377,7 +378,7 @@ def run_serve(args):
             "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": f"serve{args.serve}: Poisson arrivals at {rate:.2f}/s over 8 meshes "
                                    "(44..399 squared x 24 layers, z-jitter 0.3), eps in {1e-4,1e-3,1e-2,1e-1}, "
-                                   "Neumann/Dirichlet-top 50/50, 1-8 RHS per request, 8-slot engines, rtol 1e-8",
+                                   f"Neumann/Dirichlet-top 50/50, 1-8 RHS per request, {args.slots}-slot engines, rtol 1e-8",
                        "precision": args.precision},
             "p50_latency_ms": p["p50_latency_ms"], "p99_latency_ms": p["p99_latency_ms"],
             "requests_per_s": p["requests_per_s"], "serving": out}

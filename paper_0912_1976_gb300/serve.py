@@ -85,7 +85,7 @@ class Server:
         self.reserve, self.iters_per_step, self.keep_x, self.clock = reserve, iters_per_step, keep_x, clock
         self.new_x = new_x
         self.cache: Dict[tuple, Entry] = collections.OrderedDict()
-        self.stats = dict(builds=0, evictions=0, deferred=0, peak_resident=0, hits=0)
+        self.stats = dict(builds=0, build_s=0.0, evictions=0, deferred=0, peak_resident=0, hits=0)
 
     # ---- memory ---------------------------------------------------------------------------
     def resident_bytes(self) -> int:
@@ -119,7 +119,9 @@ class Server:
         if not self._make_room(need):
             self.stats["deferred"] += 1
             return None
+        t0 = time.perf_counter()
         h, eng, nbytes, n = self.build(key)
+        self.stats["build_s"] += time.perf_counter() - t0   # mesh assembly + setup, host clock
         e = Entry(key, h, eng, nbytes, n, now)
         self.cache[key] = e
         self.stats["builds"] += 1
