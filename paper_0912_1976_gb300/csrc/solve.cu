@@ -28,7 +28,7 @@ namespace vemg {
 static constexpr int kRedBlocks = 608;  // 4 x 152 SMs
 static constexpr int kRedThreads = 256;
 static constexpr int kSellBlock = 128;  // 4 slices per block
-static constexpr int kRows = 4;         // rows per thread and loop trip in the streaming kernels
+static constexpr int kRows = 1;         // rows per thread and loop trip in the streaming kernels (1: k_combine fits 4 blocks per SM)
 static constexpr int kEmax = 4;         // E~ rows with at most this many entries take the fast path
 
 // ------------------------------------------------------------------------------------------
