@@ -463,8 +463,9 @@ static SellArgs sargs(const Sell &S) {
     return SellArgs{S.nslices, S.row0, S.nrow, S.off, S.width, S.col, (const double *)S.v};
 }
 
-// q = A p over all slices and (p, q); the last block sets alpha = rz / pq
-__global__ void __launch_bounds__(kRedThreads) k_spmv_pq(SellArgs A, const double *__restrict__ p,
+// q = A p over all slices and (p, q); the last block sets alpha = rz / pq. At most 64 registers:
+// the whole grid (kRedBlocks = 4 per SM) is resident at once.
+__global__ void __launch_bounds__(kRedThreads, kRedBlocks / 152) k_spmv_pq(SellArgs A, const double *__restrict__ p,
                                                          double *__restrict__ q, double *sc, double *part,
                                                          unsigned *ctr, double *coef) {
     pdl_begin();
