@@ -1262,9 +1262,11 @@ static void colour_level(Arena &ar, Level &L, cudaStream_t s) {
     }
     // peeling: raise the threshold whenever the worklist runs empty, else kRoundBatch rounds per
     // host check (rounds after an empty worklist do nothing; their ranks stay unused, which
-    // keeps the order of the ranks)
+    // keeps the order of the ranks). Every batch removes a node (a raise guarantees one in its
+    // first round): the bound on the batches turns a broken invariant into an error, not a hang.
     int t = 0, k = 0;
-    while (n > 0 && read_int(removed, s) < n) {
+    for (int64_t batches = 0; n > 0 && read_int(removed, s) < n; ++batches) {
+        if (batches > 2 * (int64_t)n + 64) throw Error{VEMG_EINTERNAL};
         if (read_int(nring + t % kRing, s) == 0) {
             VEMG_CHECK_CUDA(cudaMemsetAsync(dmin, 0x7f, sizeof(int), s));
             k_peel_min<<<grid_for(n, 256), 256, 0, s>>>(n, deg, rank, dmin);
@@ -1284,7 +1286,9 @@ static void colour_level(Arena &ar, Level &L, cudaStream_t s) {
         k_jp_pred<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, rank, pc, wl[0], nring);
         VEMG_CHECK_LAUNCH();
     }
-    for (t = 0; n > 0;) {
+    t = 0;   // the colouring's first worklist sits in slot 0 of the ring
+    for (int64_t batches = 0; n > 0; ++batches) {
+        if (batches > (int64_t)n + 64) throw Error{VEMG_EINTERNAL};   // every batch colours a node
         for (int u = 0; u < kRoundBatch; ++u, ++t)
             k_jp_round<<<kRoundBlocks, kRoundThreads, 0, s>>>(wl[t & 1], wl[(t + 1) & 1], nring, t, L.A.rp, L.A.ci,
                                                               rank, pc, L.colour, maxc);
