@@ -407,6 +407,39 @@ def test_colouring_of_paths_stars_cliques():
     assert nc == 6 and sorted(col.tolist()) == list(range(6))
 
 
+def test_jones_plassmann_rounds_equal_greedy_in_key_order():
+    """The GPU colours by Jones-Plassmann rounds on fixed keys, the oracle greedily in decreasing
+    key order: with distinct keys both give the same colouring (a node is coloured exactly when
+    its larger-key neighbours are). Checked on random graphs with random distinct keys."""
+    rng = np.random.default_rng(21)
+    for trial in range(30):
+        n = int(rng.integers(2, 60))
+        edges = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < rng.uniform(0.05, 0.4)]
+        nb = [set() for _ in range(n)]
+        for a, b in edges:
+            nb[a].add(b)
+            nb[b].add(a)
+        key = rng.permutation(n)
+
+        def first_fit(i, col):
+            used = {col[j] for j in nb[i] if col[j] >= 0}
+            c = 0
+            while c in used:
+                c += 1
+            return c
+
+        greedy = [-1] * n
+        for i in sorted(range(n), key=lambda i: -key[i]):
+            greedy[i] = first_fit(i, greedy)
+        jp = [-1] * n
+        while min(jp) < 0:
+            win = [i for i in range(n) if jp[i] < 0 and all(jp[j] >= 0 or key[j] < key[i] for j in nb[i])]
+            new = {i: first_fit(i, jp) for i in win}
+            for i, c in new.items():
+                jp[i] = c
+        assert jp == greedy
+
+
 def test_colour_count_within_degeneracy_bound_and_clique_bound():
     """Smallest-last greedy uses at most degeneracy + 1 colours (degeneracy = the largest k with a
     non-empty k-core, from networkx); every tetrahedron is a 4-clique of the level-0 graph, so
