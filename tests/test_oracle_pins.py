@@ -407,6 +407,43 @@ def test_colouring_of_paths_stars_cliques():
     assert nc == 6 and sorted(col.tolist()) == list(range(6))
 
 
+def test_worklist_peeling_gives_the_same_rank_order():
+    """The GPU peels on worklists: a round removes its worklist, a neighbour joins the next one
+    when its degree falls from k + 1 to k, and an empty worklist raises k to the smallest remaining
+    degree (its round index then goes unused). Simulated here, the rank order must equal the
+    oracle's round-synchronous ranks."""
+    rng = np.random.default_rng(22)
+    for trial in range(30):
+        n = int(rng.integers(1, 50))
+        edges = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < rng.uniform(0.05, 0.5)]
+        A = _graph(n, edges)
+        nb = [set() for _ in range(n)]
+        for a, b in edges:
+            nb[a].add(b)
+            nb[b].add(a)
+        deg = [len(nb[i]) for i in range(n)]
+        rank = [-1] * n
+        k, t, wl, removed = 0, 0, [], 0
+        while removed < n:
+            if not wl:   # raise
+                k = max(k, min(deg[i] for i in range(n) if rank[i] < 0))
+                wl = [i for i in range(n) if rank[i] < 0 and deg[i] <= k]
+                t += 1   # the empty round's index goes unused
+            nxt = []
+            for v in wl:
+                rank[v] = t
+            for v in wl:
+                for j in nb[v]:
+                    if rank[j] < 0:
+                        deg[j] -= 1
+                        if deg[j] == k:
+                            nxt.append(j)
+            removed += len(wl)
+            wl, t = nxt, t + 1
+        dense = np.unique(np.array(rank), return_inverse=True)[1]
+        assert dense.tolist() == O.sl_ranks(A).tolist()
+
+
 def test_jones_plassmann_rounds_equal_greedy_in_key_order():
     """The GPU colours by Jones-Plassmann rounds on fixed keys, the oracle greedily in decreasing
     key order: with distinct keys both give the same colouring (a node is coloured exactly when
