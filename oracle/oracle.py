@@ -63,6 +63,8 @@ def lib():
         L.or_vcycle.argtypes = [C.c_void_p, C.c_int, dp, dp]
         L.or_sa_aggregate.argtypes = [C.c_int, ip, ip, dp, C.c_double, C.c_int, ip]
         L.or_colour.argtypes = [C.c_int, ip, ip, ip]
+        L.or_smoothed_prolongator.argtypes = [C.c_int, ip, ip, dp, ip, C.c_int, C.c_double, C.c_double, ip, ip,
+                                              dp, C.c_int]
         L.or_sl_ranks.argtypes = [C.c_int, ip, ip, ip]
         L.or_locate_points.argtypes = [C.c_int, ip, dp, C.c_int, dp, ip, dp]
         L.or_elem_stiffness.restype = C.c_double
@@ -215,6 +217,24 @@ def sa_aggregate(A: sp.csr_matrix, theta=THETA, keep_isolated=True):
     nagg = lib().or_sa_aggregate(A.shape[0], _p(rp, C.c_int), _p(ci, C.c_int), _p(v, C.c_double), theta,
                                  int(keep_isolated), _p(agg, C.c_int))
     return nagg, agg
+
+
+def smoothed_prolongator(A: sp.csr_matrix, agg, nagg, omega=OMEGA_P, theta=THETA):
+    """The smoothed prolongator of the given aggregates (agg[i] = -1: unaggregated row)."""
+    A = A.tocsr()
+    A.sort_indices()
+    n = A.shape[0]
+    rp, ci, v, ag = _i32(A.indptr), _i32(A.indices), _f64(A.data), _i32(agg)
+    cap = max(int(A.nnz) + n, 1)
+    prp = np.zeros(n + 1, np.int32)
+    pci = np.zeros(cap, np.int32)
+    pv = np.zeros(cap)
+    nnz = lib().or_smoothed_prolongator(n, _p(rp, C.c_int), _p(ci, C.c_int), _p(v, C.c_double), _p(ag, C.c_int),
+                                        int(nagg), omega, theta, _p(prp, C.c_int), _p(pci, C.c_int),
+                                        _p(pv, C.c_double), cap)
+    if nnz < 0:
+        raise OracleError("prolongator capacity")
+    return sp.csr_matrix((pv[:nnz], pci[:nnz], prp), shape=(n, int(nagg)))
 
 
 def colour(A: sp.csr_matrix):

@@ -592,6 +592,23 @@ static csr smoothed_prolongator(const csr *A, const int *agg, int nagg, double o
     return P;
 }
 
+/* exported for the closed-form tests of the prolongator weights: P of the given aggregates
+   (agg[i] = -1: unaggregated) written to prp (n + 1), pci and pv (cap entries at most).
+   Returns the number of entries, or -1 when cap is too small. */
+int or_smoothed_prolongator(int n, const int *rp, const int *ci, const double *v, const int *agg, int nagg,
+                            double omega, double theta, int *prp, int *pci, double *pv, int cap) {
+    csr A;
+    A.n = n; A.m = n; A.rp = (int *)rp; A.ci = (int *)ci; A.v = (double *)v;
+    csr P = smoothed_prolongator(&A, agg, nagg, omega, theta);
+    int nnz = csr_nnz(&P);
+    if (nnz > cap) { csr_del(&P); return -1; }
+    memcpy(prp, P.rp, sizeof(int) * ((size_t)n + 1));
+    memcpy(pci, P.ci, sizeof(int) * (size_t)nnz);
+    memcpy(pv, P.v, sizeof(double) * (size_t)nnz);
+    csr_del(&P);
+    return nnz;
+}
+
 static void level_colour(level *L) {
     int n = L->A.n;
     L->colour = (int *)xcalloc((size_t)n, sizeof(int));

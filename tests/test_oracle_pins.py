@@ -343,6 +343,85 @@ def test_chain_drops_isolated_rows_on_a_bar_only():
         assert np.all(P.ints("lev.agg", 0, l) >= 0)
 
 
+def _path_with_weak_link(n, end_diag, weak=1e-3, link=(4, 7)):
+    """1D Laplacian [-1, 2, -1] on a path of n nodes with end diagonals end_diag (1: Neumann ends,
+    A 1 = 0; 2: Dirichlet ends, non-singular like A_bar), plus one weak symmetric coupling -weak
+    between the nodes of `link`, its value lumped into their diagonals (row sums unchanged)."""
+    A = _lap1d(n).tolil()
+    A[0, 0] = A[n - 1, n - 1] = end_diag
+    i, j = link
+    A[i, j] = A[j, i] = -weak
+    A[i, i] += weak
+    A[j, j] += weak
+    return A.tocsr()
+
+
+@pytest.mark.parametrize("end_diag", [1.0, 2.0])
+def test_smoothed_prolongator_closed_form_on_a_path(end_diag):
+    """P = (I - omega (D^F)^-1 A^F) P_tent with omega = 2/3 (section 6) on a path with aggregates
+    {0,1,2}, {3,4,5}, {6,7,8}, by hand:
+      - a node inside its aggregate keeps the single entry 1 (its A row sums to 0 inside it);
+      - a node at an aggregate boundary of [-1, 2, -1]: (D^-1 A P_tent) = (1/2, -1/2), so
+        P = (1 - 2/3 * 1/2, 2/3 * 1/2) = (2/3, 1/3) on (own, neighbour) aggregate;
+      - nodes 4 and 7 carry a weak coupling (-1e-3, below 0.01 sqrt(A_ii A_jj)): the filtered
+        matrix drops it and lumps it into the diagonal (A^F_ii = A_ii - 1e-3 = 2), so their rows
+        are exactly those of the plain path: 1 on their own aggregate and no entry on the other;
+      - a Dirichlet end (diagonal 2, one neighbour): (D^-1 A P_tent) = 1/2 on its aggregate, so
+        P = 1 - 1/3 = 2/3 (the row does not sum to 1: P 1 = 1 holds only where A 1 = 0).
+    A wrong omega, a missing D^-1, the unfiltered matrix or the lumped value with the wrong sign
+    each changes one of these entries."""
+    A = _path_with_weak_link(9, end_diag)
+    agg = np.repeat(np.arange(3), 3)
+    P = O.smoothed_prolongator(A, agg, 3).toarray()
+    t = 2.0 / 3.0
+    e = 1.0 - t * (end_diag - 1.0) / end_diag          # 1 at a Neumann end, 2/3 at a Dirichlet end
+    ref = np.array([[e, 0, 0], [1, 0, 0], [t, 1 - t, 0],
+                    [1 - t, t, 0], [0, 1, 0], [0, t, 1 - t],
+                    [0, 1 - t, t], [0, 0, 1], [0, 0, e]])
+    assert np.abs(P - ref).max() <= 1e-15
+    # the weak link leaves no stored entry on the other aggregate
+    Ps = O.smoothed_prolongator(A, agg, 3)
+    assert list(Ps[4].indices) == [1] and list(Ps[7].indices) == [2]
+
+
+def test_smoothed_prolongator_unaggregated_and_isolated_rows():
+    """An unaggregated row (agg = -1) is empty; an aggregated row with no strong coupling keeps its
+    tentative row (nothing to smooth against); omega enters linearly."""
+    n = 6
+    A = sp.block_diag([_lap1d(n), sp.diags([4.0, 5.0])]).tolil()
+    A[0, n] = A[n, 0] = -0.001
+    A[0, 0] += 0.001
+    A[n, n] += 0.001
+    A = A.tocsr()
+    agg = np.array([0, 0, 0, 1, 1, 1, 2, -1])
+    P = O.smoothed_prolongator(A, agg, 3)
+    assert P[7].nnz == 0
+    assert list(P[6].indices) == [2] and P[6].data[0] == 1.0
+    # omega = 1/3 at the boundary node 2: (1 - 1/6, 1/6)
+    Pw = O.smoothed_prolongator(A, agg, 3, omega=1.0 / 3.0).toarray()
+    assert np.abs(Pw[2, :2] - [5.0 / 6.0, 1.0 / 6.0]).max() <= 1e-15
+    # the Dirichlet-like end 0 (diagonal 2.001 filtered back to 2, one neighbour in its aggregate)
+    P2 = P.toarray()
+    assert abs(P2[0, 0] - (1.0 - (2.0 / 3.0) * 0.5)) <= 1e-15
+
+
+def test_chain_prolongators_are_the_smoothed_prolongator_with_omega_two_thirds():
+    """Every level's P in the setup chains is the smoothed prolongator (pinned above) of that
+    level's operator and aggregates with the paper's omega = 2/3 and strength 0.01: the chains
+    pass the section-6 parameters through."""
+    m = _mesh(10, 6, h0=1e-3, zj=0.3)
+    P = O.Problem(m)
+    for which in (0, 1):
+        for l in range(P.nlev(which) - 1):
+            A = P.csr("lev.A", which, l)
+            agg = P.ints("lev.agg", which, l)
+            nagg = P.size("lev.n", which, l + 1)
+            ref = O.smoothed_prolongator(A, agg, nagg, omega=2.0 / 3.0, theta=0.01)
+            got = P.csr("lev.P", which, l)
+            assert np.array_equal(got.indptr, ref.indptr) and np.array_equal(got.indices, ref.indices)
+            assert np.array_equal(got.data, ref.data)
+
+
 def test_colouring_is_proper():
     m = _mesh(6, 4, zj=0.3)
     P = O.Problem(m)
