@@ -292,17 +292,23 @@ int vemg_precond(vemg_hierarchy *h, const double *r_dev, double *z_dev, void *st
 /* One V-cycle of chain `chain` from a zero initial guess on its finest level (device). */
 int vemg_vcycle(vemg_hierarchy *h, int chain, const double *b_dev, double *x_dev, void *stream);
 
-/* y = A x exactly as vemg_spmv computes it, but allocating no device memory. (The paper has no
-   counterpart: this serves callers that cannot call cudaMalloc, such as code running inside an
-   allocator callback, or a process whose device memory budget is fixed before the solve starts.)
+/* y = A x exactly as vemg_spmv computes it (the same products summed in the same order, so the
+   same bits), but allocating no device memory. (The paper has no counterpart: this serves
+   callers that cannot call cudaMalloc, such as code running inside an allocator callback, or a
+   process whose device memory budget is fixed before the solve starts.)
+   The hierarchy must already hold its solve layout: the first vemg_solve, vemg_solve_host,
+   vemg_spmv or vemg_precond on a hierarchy builds it (allocating), so make one of those calls
+   once, at a point where allocation is allowed, before the first vemg_spmv_static. Without it the
+   call returns VEMG_EINVAL and vemg_last_error says so.
    Its work buffers live in one static device array owned by the library: 12 MiB, enough for
-   hierarchies of at most 1,048,576 unknowns; larger hierarchies are rejected with VEMG_EINVAL.
-   Every device that loads libvemg holds that array until the process exits. The first call on a
-   device looks up the array's device address (cudaGetSymbolAddress) with that device current;
-   make that first call before any stream capture. All calls share the one array: calls whose
-   GPU work overlaps (several streams or host threads at once) race and give wrong results. The
-   array needs no clearing: each call writes every entry it later reads. x_dev and y_dev are
-   device arrays in the internal order, as for vemg_spmv. Synchronises the stream. */
+   hierarchies of at most 1,048,576 unknowns; a larger hierarchy is rejected with VEMG_EINVAL
+   (vemg_last_error gives the count). Every device that loads libvemg holds that array until the
+   process exits. The first call on a device looks up the array's device address
+   (cudaGetSymbolAddress) with that device current; make that first call before any stream
+   capture. All calls share the one array: calls whose GPU work overlaps (several streams or host
+   threads at once) race and give wrong results. The array needs no clearing: each call writes
+   every entry it later reads. x_dev and y_dev are device arrays in the internal order, as for
+   vemg_spmv. Each call synchronises the stream (cudaStreamSynchronize) before it returns. */
 int vemg_spmv_static(vemg_hierarchy *h, const double *x_dev, double *y_dev, void *stream);
 
 /* ---- measurement ---- */

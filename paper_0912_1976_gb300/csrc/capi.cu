@@ -23,6 +23,8 @@ void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int 
 
 const char *last_cuda_error() { return g_cuda_err; }
 
+void set_last_error_message(const char *msg) { snprintf(g_cuda_err, sizeof(g_cuda_err), "%s", msg); }
+
 // ------------------------------------------------------------------------------------------
 // allocator: every block remembers the allocator that made it
 

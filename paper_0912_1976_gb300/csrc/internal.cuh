@@ -34,6 +34,7 @@ struct Error {
 
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 const char *last_cuda_error();
+void set_last_error_message(const char *msg);   // a library-side reason behind a status code
 
 inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
 

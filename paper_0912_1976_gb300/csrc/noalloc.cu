@@ -7,6 +7,8 @@
 // vemg_spmv_static computes the same product with its work buffers in one file-scope device
 // array of fixed size instead. The array belongs to the library: every device that loads
 // libvemg holds it until the process exits.
+#include <stdio.h>
+
 #include <mutex>
 
 #include "internal.cuh"
@@ -66,19 +68,27 @@ __global__ void k_static_spmv(int nsl, const int *__restrict__ row0, const int *
     y[s2i[row0[s] + lane]] = acc;
 }
 
-}  // namespace vemg
-
-using namespace vemg;
-
-extern "C" int vemg_spmv_static(vemg_hierarchy *h, const double *x_dev, double *y_dev, void *stream) {
-    if (!h || !x_dev || !y_dev || !h->caller_of) return VEMG_EINVAL;
-    if (h->nu > kStaticMaxUnknowns) return VEMG_EINVAL;
+static int spmv_static(vemg_hierarchy *h, const double *x_dev, double *y_dev, cudaStream_t s) {
+    if (!h || !x_dev || !y_dev) return VEMG_EINVAL;
+    if (!h->caller_of) {
+        // the solve-order layout (index map and sliced-ELL operator) is built, with allocations,
+        // by the first vemg_solve, vemg_spmv or vemg_precond on the hierarchy
+        set_last_error_message("vemg_spmv_static: the hierarchy has no solve layout yet; call vemg_solve, "
+                               "vemg_spmv or vemg_precond on it once first");
+        return VEMG_EINVAL;
+    }
+    if (h->nu > kStaticMaxUnknowns) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "vemg_spmv_static: %d unknowns, more than the %d its static work array holds",
+                 h->nu, kStaticMaxUnknowns);
+        set_last_error_message(msg);
+        return VEMG_EINVAL;
+    }
     void *base = nullptr;
     int rc = static_scratch(&base);
     if (rc != VEMG_OK) return rc;
     int *s2i = (int *)base;
     double *xs = (double *)((unsigned char *)base + (size_t)kStaticMaxUnknowns * sizeof(int));
-    cudaStream_t s = (cudaStream_t)stream;
     const int nu = h->nu, off = h->bc == VEMG_DIRICHLET_TOP ? h->mtop : 0;
     k_static_gather<<<grid_for(nu, 256), 256, 0, s>>>(nu, off, h->caller_of, h->old2new, x_dev, s2i, xs);
     cudaError_t e = cudaGetLastError();
@@ -95,4 +105,17 @@ extern "C" int vemg_spmv_static(vemg_hierarchy *h, const double *x_dev, double *
         return VEMG_ECUDA;
     }
     return VEMG_OK;
+}
+
+}  // namespace vemg
+
+using namespace vemg;
+
+extern "C" int vemg_spmv_static(vemg_hierarchy *h, const double *x_dev, double *y_dev, void *stream) {
+    // no C++ exception crosses the ABI (the helpers above throw none; this is the backstop)
+    try {
+        return spmv_static(h, x_dev, y_dev, (cudaStream_t)stream);
+    } catch (...) {
+        return VEMG_EINTERNAL;
+    }
 }

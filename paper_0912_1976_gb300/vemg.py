@@ -454,7 +454,11 @@ def vemg_spmv_static(h: Hierarchy, x_dev, y_dev=None, stream=None):
     """y = A x with no device allocation (work buffers in the library's static device array)."""
     if y_dev is None:
         y_dev = torch.empty_like(x_dev)
-    _check(lib().vemg_spmv_static(h.h, _dev(x_dev), _dev(y_dev), _stream(stream)), "vemg_spmv_static")
+    rc = lib().vemg_spmv_static(h.h, _dev(x_dev), _dev(y_dev), _stream(stream))
+    if rc != VEMG_OK:
+        err = VemgError(rc, "vemg_spmv_static")
+        err.detail = (lib().vemg_last_error() or b"").decode(errors="replace")
+        raise err
     return y_dev
 
 
