@@ -329,8 +329,9 @@ def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe, cycle="launch
             kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "sor_fine": V.VEMG_PROBE_SOR_FINE,
                      "vcycle_coarse": V.VEMG_PROBE_VCYCLE}
         else:
-            kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "sor_fine": V.VEMG_PROBE_SOR_FINE, "sor_all": V.VEMG_PROBE_SOR,
-                     "residual": V.VEMG_PROBE_RESIDUAL}
+            kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "sor_fine": V.VEMG_PROBE_SOR_FINE,
+                     "sor_coarse": V.VEMG_PROBE_SOR_COARSE, "residual": V.VEMG_PROBE_RESIDUAL,
+                     "transfer": V.VEMG_PROBE_TRANSFER, "vector": V.VEMG_PROBE_VECTOR, "dense": V.VEMG_PROBE_DENSE}
         for name, kind in kinds.items():
             V.vemg_probe(h, kind)
             for j in range(2):
@@ -340,7 +341,8 @@ def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe, cycle="launch
             if r["launches"]:
                 classes[name] = {"launches_per_solve": r["launches"] / 2, "ms_per_solve": r["ms"] / 2,
                                  "achieved_gbs": r["bytes"] / (r["ms"] / 1000.0) / 1e9,
-                                 "bytes_per_launch": r["bytes"] / r["launches"]}
+                                 "bytes_per_launch": r["bytes"] / r["launches"],
+                                 "bytes_per_solve": r["bytes"] / 2}
     out["classes"] = classes
     return out
 
@@ -563,7 +565,10 @@ def main():
     roofline = None
     classes = head["classes"]
     if classes:
-        dom = max((c for c in classes if c != "sor_all"), key=lambda c: classes[c]["ms_per_solve"])
+        # the dominant class: the largest share of the probed (event-timed, serialised) device time
+        dom = max(classes, key=lambda c: classes[c]["ms_per_solve"])
+        for c in classes.values():
+            c["frac"] = c["achieved_gbs"] / hbm
         c = classes[dom]
         # DRAM traffic per launch of the finest-level colour sweep, from one ncu capture on a
         # 192x192x32 mesh (colour 2, 261,577 rows): 1.07 (FP32 values) / 1.09 (BF16 values) x its
@@ -573,9 +578,16 @@ def main():
             traffic = {"bytes_per_launch": SOR_FINE_DRAM_RATIO[args.precision] * c["bytes_per_launch"],
                        "source": f"ncu dram__bytes (read + write) of one {SOR_FINE_KERNEL[args.precision]} launch "
                                  "on a 192x192x32 mesh, scaled by algorithmic bytes per launch"}
+        # the whole solve: every class's algorithmic bytes over the un-probed time of a solve
+        solve_bytes = sum(x["bytes_per_solve"] for x in classes.values())
+        whole = solve_bytes / (head["ms_per_step"] / 1000.0) / 1e9
         roofline = {"bound": "hbm", "kernel": dom, "achieved": c["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                     "frac": c["achieved_gbs"] / hbm, "peak_source": f"{peak_kind} hbm_gbs (copy, burst)",
-                    "traffic": traffic, "classes": classes}
+                    "traffic": traffic,
+                    "share_of_probed_time": c["ms_per_solve"] / sum(x["ms_per_solve"] for x in classes.values()),
+                    "whole_solve": {"algorithmic_bytes_per_solve": solve_bytes, "achieved_gbs": whole,
+                                    "frac": whole / hbm},
+                    "classes": classes}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -296,10 +296,8 @@ int vemg_vcycle(vemg_hierarchy *h, int chain, const double *b_dev, double *x_dev
    same bits), but allocating no device memory. (The paper has no counterpart: this serves
    callers that cannot call cudaMalloc, such as code running inside an allocator callback, or a
    process whose device memory budget is fixed before the solve starts.)
-   The hierarchy must already hold its solve layout: the first vemg_solve, vemg_solve_host,
-   vemg_spmv or vemg_precond on a hierarchy builds it (allocating), so make one of those calls
-   once, at a point where allocation is allowed, before the first vemg_spmv_static. Without it the
-   call returns VEMG_EINVAL and vemg_last_error says so.
+   vemg_setup builds everything this call reads (the solve-order index map and operator), so it
+   works on any hierarchy vemg_setup returned, before or after any solve.
    Its work buffers live in one static device array owned by the library: 12 MiB, enough for
    hierarchies of at most 1,048,576 unknowns; a larger hierarchy is rejected with VEMG_EINVAL
    (vemg_last_error gives the count). Every device that loads libvemg holds that array until the
@@ -319,10 +317,15 @@ int vemg_kernel_launches(const vemg_hierarchy *h, int64_t *count);
 /* Kernel classes that vemg_probe can time. */
 #define VEMG_PROBE_NONE 0
 #define VEMG_PROBE_SPMV_A 1      /* q = A p of the outer Krylov loop */
-#define VEMG_PROBE_SOR 2         /* every multicolour SOR launch of both chains */
+#define VEMG_PROBE_SOR_COARSE 2  /* multicolour SOR launches on every level except the finest
+                                    level of the A_bar chain (every level of the other chains) */
+#define VEMG_PROBE_SOR VEMG_PROBE_SOR_COARSE   /* the same class under its earlier name */
 #define VEMG_PROBE_RESIDUAL 3    /* every V-cycle residual launch */
 #define VEMG_PROBE_SOR_FINE 4    /* SOR launches on the finest level of the A_bar chain */
 #define VEMG_PROBE_VCYCLE 5      /* the persistent preconditioner kernel (VEMG_CYCLE_PERSISTENT) */
+#define VEMG_PROBE_TRANSFER 6    /* restrictions, prolongations and E~^T r (sliced-ELL transfers) */
+#define VEMG_PROBE_VECTOR 7      /* the Krylov vector kernels: x/r update, z combination, p update */
+#define VEMG_PROBE_DENSE 8       /* the dense coarsest-level solves */
 
 /* Start timing one kernel class (VEMG_PROBE_NONE stops): every later launch of that class
    records a CUDA event before and after itself on its stream. Resets the accumulated totals. */

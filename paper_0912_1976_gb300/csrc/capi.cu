@@ -447,7 +447,7 @@ int vemg_kernel_launches(const vemg_hierarchy *h, int64_t *count) {
 
 int vemg_probe(vemg_hierarchy *h, int kind) {
     return guarded([&] {
-        if (!h || kind < VEMG_PROBE_NONE || kind > VEMG_PROBE_VCYCLE) return VEMG_EINVAL;
+        if (!h || kind < VEMG_PROBE_NONE || kind > VEMG_PROBE_DENSE) return VEMG_EINVAL;
         probe_start(h, kind);
         if (kind == VEMG_PROBE_VCYCLE) persist_profile_reset(h);
         return VEMG_OK;

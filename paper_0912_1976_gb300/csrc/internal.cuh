@@ -138,7 +138,8 @@ struct Level {
 // Opt-in timing of one kernel class: CUDA events recorded on the launching stream around each
 // launch, plus the algorithmic bytes of each launch (bytes the operation must move at minimum).
 enum ProbeKind {
-    PROBE_NONE = 0, PROBE_SPMV_A = 1, PROBE_SOR = 2, PROBE_RESIDUAL = 3, PROBE_SOR_FINE = 4, PROBE_VCYCLE = 5
+    PROBE_NONE = 0, PROBE_SPMV_A = 1, PROBE_SOR = 2, PROBE_RESIDUAL = 3, PROBE_SOR_FINE = 4, PROBE_VCYCLE = 5,
+    PROBE_TRANSFER = 6, PROBE_VECTOR = 7, PROBE_DENSE = 8
 };
 
 struct Probe {

@@ -71,10 +71,9 @@ __global__ void k_static_spmv(int nsl, const int *__restrict__ row0, const int *
 static int spmv_static(vemg_hierarchy *h, const double *x_dev, double *y_dev, cudaStream_t s) {
     if (!h || !x_dev || !y_dev) return VEMG_EINVAL;
     if (!h->caller_of) {
-        // the solve-order layout (index map and sliced-ELL operator) is built, with allocations,
-        // by the first vemg_solve, vemg_spmv or vemg_precond on the hierarchy
-        set_last_error_message("vemg_spmv_static: the hierarchy has no solve layout yet; call vemg_solve, "
-                               "vemg_spmv or vemg_precond on it once first");
+        // vemg_setup builds the solve-order layout (index map and sliced-ELL operator); a
+        // hierarchy without it did not come from a successful vemg_setup
+        set_last_error_message("vemg_spmv_static: the hierarchy has no solve layout (not set up)");
         return VEMG_EINVAL;
     }
     if (h->nu > kStaticMaxUnknowns) {

@@ -279,6 +279,13 @@ static void sell_spmv(const Sell &S, const XT *x, YT *y, int add, cudaStream_t s
     const YT *d0 = first ? (const YT *)first->dinv : nullptr;
     YT *x0 = first ? (YT *)first->x : nullptr;
     const int lim0 = first ? first->crow[1] : 0;
+    // stored entries, y written (and read when adding), x read once; the fused first colour reads
+    // its inverse diagonal and writes its x
+    const double vb = S.vh ? 2.0 : (double)(S.fp32 ? 4 : 8);
+    ProbeScope ps(PROBE_TRANSFER,
+                  sell_bytes(S.nnz, vb, S.n, (add ? 2.0 : 1.0) * sizeof(YT)) + (double)sizeof(XT) * S.m +
+                      2.0 * sizeof(YT) * lim0,
+                  s);
     if (S.vh)   // BF16 values (FP32 vectors)
         pdl_launch(k_sell_spmv<__nv_bfloat16, XT, YT, AT>, grid_for(threads, kSellBlock), kSellBlock, s, 0,
                    S.nslices, S.row0, S.nrow, S.off, S.width, S.col, (const __nv_bfloat16 *)S.vh, x, y, add, d0, x0,
@@ -360,6 +367,7 @@ static void vcycle_level(const SChain &C, int l, const BT *b, XT *x, cudaStream_
     if (l == C.nlev - 1) {
         if (C.direct) {
             const XT *G = sizeof(XT) == sizeof(float) ? (const XT *)C.Gf : (const XT *)C.G;
+            ProbeScope ps(PROBE_DENSE, (double)sizeof(XT) * C.nc * (C.nc + 1.0) + (double)sizeof(BT) * C.nc, s);
             pdl_launch(k_dense_mv<XT, BT>, grid_for(C.nc, 8), 256, s, C.nc, G, b, x);
             SOLVE_LAUNCHED();
             return;
@@ -742,7 +750,8 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
     const XT *ys = nullptr;
     // probes of the per-phase kernel classes time the launch-per-phase cycle
     const int pk = h->probe.kind;
-    const bool persist = h->persist && pk != PROBE_SOR && pk != PROBE_SOR_FINE && pk != PROBE_RESIDUAL;
+    const bool persist = h->persist && pk != PROBE_SOR && pk != PROBE_SOR_FINE && pk != PROBE_RESIDUAL &&
+                         pk != PROBE_TRANSFER && pk != PROBE_DENSE;
     const bool none = h->precond == VEMG_PRECOND_NONE;
     const bool hybrid = persist && persist_coarse_only(h);
     if (none) {
@@ -802,6 +811,13 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
         if (two) VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
     }
     const XT *xb = none ? (const XT *)r : (const XT *)B.lv[0].x;   // none: XT is double
+    // r, z (and q) per row, x_bar per non-top row, the E~ entries and one read of y_s
+    ProbeScope ps(PROBE_VECTOR,
+                  (double)h->nu * (16.0 + (flex && !first ? 8.0 : 0.0)) + (double)(h->nu - mt) * sizeof(XT) +
+                      (two ? sell_bytes(h->Enon.nnz, h->Enon_vf && sizeof(XT) == 4 ? 4.0 : 8.0, 0, 0.0) +
+                                 (double)sizeof(XT) * mt
+                           : 0.0),
+                  s);
     pdl_launch(k_combine<XT>, kRedBlocks, kRedThreads, s, h->nu, mt, sargs(h->Enon), (const float *)h->Enon_vf, ys, xb, z, r,
                                                      h->q, neu, flex, first, 1.0 / (double)h->nu, h->scal,
                                                      h->red + 5 * kRedBlocks * C_Z, h->ctr + C_Z,
@@ -870,13 +886,17 @@ static void phase_pre(vemg_hierarchy *h, cudaStream_t s) {
                                                  h->ctr + C_PREP);
     SOLVE_LAUNCHED();
     precond_solve_order(h, h->r, h->z, 1, s);
-    pdl_launch(k_update_p, grid_for(nu, 256), 256, s, nu, h->scal, h->z, h->p);
-    SOLVE_LAUNCHED();
+    {
+        ProbeScope ps(PROBE_VECTOR, 24.0 * nu, s);   // z, p read; p written
+        pdl_launch(k_update_p, grid_for(nu, 256), 256, s, nu, h->scal, h->z, h->p);
+        SOLVE_LAUNCHED();
+    }
 }
 
 // q = A p, alpha, x and r updates, ||r||, continuation
 static void phase_step(vemg_hierarchy *h, cudaStream_t s, cudaGraphConditionalHandle hd, int use_cond) {
     spmv_outer(h, h->p, h->q, s);
+    ProbeScope ps(PROBE_VECTOR, 48.0 * h->nu, s);   // p, q, x, r read; x, r written
     pdl_launch(k_update_xr, kRedBlocks, kRedThreads, s, h->nu, h->p, h->q, h->x, h->r, h->scal, part_of(h, C_XR),
                                                    h->ctr + C_XR, hd, use_cond);
     SOLVE_LAUNCHED();
@@ -885,6 +905,7 @@ static void phase_step(vemg_hierarchy *h, cudaStream_t s, cudaGraphConditionalHa
 // new preconditioned residual and search direction
 static void phase_direction(vemg_hierarchy *h, cudaStream_t s) {
     precond_solve_order(h, h->r, h->z, 0, s);
+    ProbeScope ps(PROBE_VECTOR, 24.0 * h->nu, s);   // z, p read; p written
     pdl_launch(k_update_p, grid_for(h->nu, 256), 256, s, h->nu, h->scal, h->z, h->p);
     SOLVE_LAUNCHED();
 }

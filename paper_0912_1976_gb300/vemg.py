@@ -102,7 +102,9 @@ PROTOTYPES = {
     "vemg_probe_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "vemg_probe_phases": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), _VP, _VP, _VP, _VP]),
 }
-VEMG_PROBE_NONE, VEMG_PROBE_SPMV_A, VEMG_PROBE_SOR, VEMG_PROBE_RESIDUAL, VEMG_PROBE_SOR_FINE, VEMG_PROBE_VCYCLE = range(6)
+(VEMG_PROBE_NONE, VEMG_PROBE_SPMV_A, VEMG_PROBE_SOR_COARSE, VEMG_PROBE_RESIDUAL, VEMG_PROBE_SOR_FINE, VEMG_PROBE_VCYCLE,
+ VEMG_PROBE_TRANSFER, VEMG_PROBE_VECTOR, VEMG_PROBE_DENSE) = range(9)
+VEMG_PROBE_SOR = VEMG_PROBE_SOR_COARSE
 
 
 def lib_path() -> str:

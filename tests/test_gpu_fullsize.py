@@ -10,6 +10,7 @@ import torch
 from oracle import oracle as O
 from paper_0912_1976_gb300 import inputs as I
 from paper_0912_1976_gb300 import vemg as V
+from conftest import record
 
 pytestmark = pytest.mark.gpu
 
@@ -98,3 +99,51 @@ def test_full_size_solve_properties(precision, cycle):
     assert abs(x.mean().item()) <= 1e-12 * x.abs().max().item()
     # the method's iteration count at this size (the oracle takes 27 on the same workload)
     assert 24 <= info["iters"] <= 30
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_full_size_solution_matches_oracle():
+    """The bench workload solved on the GPU with FP64 V-cycles against the oracle's own solve of
+    the same right-hand side: iterations within one, x within 1e-9 relative L2 (after the same
+    number of iterations when the stopping test falls on different sides of rtol)."""
+    m, vm, A = _full()
+    h = V.vemg_setup(A, vm, V.vemg_default_options(precision=V.VEMG_PREC_FP64))
+    bn = I.normal_loads(m.n, 2000)
+    b = torch.from_numpy(bn).cuda()
+    x, info = V.vemg_solve(h, b, rtol=1e-8, max_it=1000)
+    om = O.Problem(m)
+    ro = om.solve(bn, tol=1e-8)
+    assert info["status"] == "OK" and ro["status"] == "OK"
+    assert abs(info["iters"] - ro["iters"]) <= 1
+    if info["iters"] == ro["iters"]:
+        err = _rel(x.cpu().numpy(), ro["x"])
+    else:
+        k = min(info["iters"], ro["iters"])
+        xk, _ = V.vemg_solve(h, b, rtol=0.0, max_it=k)
+        err = _rel(xk.cpu().numpy(), om.solve(bn, tol=0.0, maxit=k)["x"])
+    record("full_size_fp64_vs_oracle", iters_gpu=info["iters"], iters_oracle=ro["iters"], rel_l2=err)
+    assert err <= 1e-9, err
+    h.destroy()
+    # BF16 operator values (FP32 cycles in FP64 flexible CG) against the oracle running flexible
+    # CG with the same rounded operators (FP64 arithmetic): iterations within two, the true
+    # residual at the FP64 tolerance, x close to both oracle solutions
+    hb = V.vemg_setup(A, vm, V.vemg_default_options(precision=V.VEMG_PREC_BF16))
+    xb, ib = V.vemg_solve(hb, b, rtol=1e-8, max_it=1000)
+    om.round_operators_bf16()
+    rb = om.solve(bn, tol=1e-8, flexible=True)
+    err_b = _rel(xb.cpu().numpy(), rb["x"])
+    err_b64 = _rel(xb.cpu().numpy(), ro["x"])
+    err_o = _rel(rb["x"], ro["x"])
+    record("full_size_bf16_vs_oracle", iters_gpu=ib["iters"], iters_oracle_bf16=rb["iters"], rel_l2_vs_bf16_oracle=err_b,
+           rel_l2_vs_fp64_oracle=err_b64, oracle_bf16_vs_fp64=err_o, true_relres=ib["true_relres"])
+    assert ib["status"] == "OK" and rb["status"] == "OK"
+    assert abs(ib["iters"] - rb["iters"]) <= 2
+    assert ib["true_relres"] <= 2e-8
+    # measured 1.6e-11 from the oracle's BF16 solve and 2.8e-11 from its FP64 solve (27
+    # iterations each): the rounded operators change the preconditioner, not the solution
+    assert err_b <= 1e-9, err_b
+    assert err_b64 <= 1e-9, err_b64
+    hb.destroy()

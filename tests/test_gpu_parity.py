@@ -13,14 +13,16 @@ import torch
 from oracle import oracle as O
 from paper_0912_1976_gb300 import inputs as I
 from paper_0912_1976_gb300 import vemg as V
+from conftest import record
 
 pytestmark = pytest.mark.gpu
 
 # Tolerance of FP64 solve-phase parity. Both sides run the same operations in different summation
 # orders, so each result differs by a few ulps; the Krylov iteration and the coarse solves amplify
 # such differences by the conditioning of A, which grows like eps^-2 (section 4). 1e-9 holds for
-# eps >= 1e-3; the eps = 1e-4 mesh is 100x worse conditioned, so its bound is 1e-7.
-XTOL = {"box16": 1e-9, "zjit24": 1e-9, "xyjit20": 1e-7, "zjit64": 1e-9, "clust32": 1e-9}
+# eps >= 1e-3 (measured at most 1.6e-10); the eps = 1e-4 mesh is 100x worse conditioned and
+# measures 1.8e-9 after one iteration and 2.2e-9 after twelve, so its bound is 1e-8.
+XTOL = {"box16": 1e-9, "zjit24": 1e-9, "xyjit20": 1e-8, "zjit64": 1e-9, "clust32": 1e-9}
 
 CASES = {
     # the 16x16x8 thin box with flat depth 0.01 (no jitter)
@@ -135,7 +137,9 @@ def test_fixed_iteration_iterates_match(name):
         ro = om.solve(b, tol=0.0, maxit=k)
         assert ig["iters"] == ro["iters"] == k
         x, xo = xg.cpu().numpy(), ro["x"]
-        assert np.linalg.norm(x - xo) <= XTOL[name] * np.linalg.norm(xo), k
+        err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+        record("fixed_iteration_iterates_match", case=name, k=k, rel_l2=err)
+        assert err <= XTOL[name], (k, err)
         # the recursive residual norms, in units of ||b||
         assert abs(ig["relres"] - ro["relres"]) <= XTOL[name]
 
@@ -157,7 +161,15 @@ def test_converged_solve_matches(name):
     x = xg.cpu().numpy()
     assert abs(x.mean()) <= 1e-12 * np.abs(x).max()
     if ig["iters"] == ro["iters"]:
-        assert np.linalg.norm(x - ro["x"]) <= XTOL[name] * np.linalg.norm(ro["x"])
+        err = np.linalg.norm(x - ro["x"]) / np.linalg.norm(ro["x"])
+    else:
+        # the stopping test fell on different sides of tol: compare both after the same k steps
+        k = min(ig["iters"], ro["iters"])
+        xk, _ = V.vemg_solve(h, torch.from_numpy(b).cuda(), rtol=0.0, max_it=k)
+        rk = om.solve(b, tol=0.0, maxit=k)
+        err = np.linalg.norm(xk.cpu().numpy() - rk["x"]) / np.linalg.norm(rk["x"])
+    record("converged_solve_matches", case=name, iters_gpu=ig["iters"], iters_oracle=ro["iters"], rel_l2=err)
+    assert err <= XTOL[name], err
     assert ig["true_relres"] <= 2 * tol
 
 
