@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--tail-rows", type=int, default=None,
                     help="levels of at most this many rows (below the finest) run as one single-CTA kernel; "
                          "default: the library's")
+    ap.add_argument("--tail-cluster", type=int, default=None,
+                    help="CTAs of the thread-block cluster that runs the coarse tail (0: one CTA); default: the "
+                         "library's")
     ap.add_argument("--stream-path", action="store_true",
                     help="with --case: launch the solve's kernels on the stream, not from CUDA graphs")
     ap.add_argument("--rhs", type=int, default=0,
@@ -235,6 +238,7 @@ def workload_config(args, n):
                         f"all-Neumann, N(0,1) loads mean-zero, rtol {RTOL:g}",
             "precision": args.precision, "preconditioner": args.precond, "cycle": args.cycle, "rhs_per_step": kr,
             "tail_rows": args.tail_rows if args.tail_rows is not None else "default",
+            "tail_cluster": args.tail_cluster if args.tail_cluster is not None else "default",
             "l2": "inputs larger than L2 (A alone 0.39 GB; no flush needed)",
             "parallelism": f"independent problems x{args.gpus}" if args.gpus > 1 else "single GPU"}
 
@@ -331,7 +335,8 @@ def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe, cycle="launch
         else:
             kinds = {"spmv_A": V.VEMG_PROBE_SPMV_A, "sor_fine": V.VEMG_PROBE_SOR_FINE,
                      "sor_coarse": V.VEMG_PROBE_SOR_COARSE, "residual": V.VEMG_PROBE_RESIDUAL,
-                     "transfer": V.VEMG_PROBE_TRANSFER, "vector": V.VEMG_PROBE_VECTOR, "dense": V.VEMG_PROBE_DENSE}
+                     "transfer": V.VEMG_PROBE_TRANSFER, "vector": V.VEMG_PROBE_VECTOR, "dense": V.VEMG_PROBE_DENSE,
+                     "tail": V.VEMG_PROBE_TAIL}
         for name, kind in kinds.items():
             V.vemg_probe(h, kind)
             for j in range(2):
@@ -394,7 +399,8 @@ def case_phases(args, m, h, V, torch):
     from paper_0912_1976_gb300 import inputs as I
     b = torch.from_numpy(I.normal_loads(m.n, 5)).cuda()
     V.vemg_solve(h, b, rtol=RTOL)
-    V.vemg_probe(h, V.VEMG_PROBE_VCYCLE)
+    kind = V.VEMG_PROBE_TAIL if (args.tail_cluster or 0) > 0 else V.VEMG_PROBE_VCYCLE
+    V.vemg_probe(h, kind)
     _, info = V.vemg_solve(h, b, rtol=RTOL)
     r = V.vemg_probe_read(h)
     ph = V.vemg_probe_phases(h)
@@ -403,7 +409,8 @@ def case_phases(args, m, h, V, torch):
         print(json.dumps({"case": args.case, "phases": None, "note": "no persistent program (cycle is launches)"}))
         return 0
     mhz = float(os.environ.get("VEMG_SM_MHZ", "2070"))
-    napp = max(r["launches"], 1)
+    # one persistent launch per application, or one tail launch per chain per application
+    napp = max(r["launches"] // (len({p["group"] for p in ph}) if kind == V.VEMG_PROBE_TAIL else 1), 1)
     agg = {}
     for p in ph:
         k = (p["group"], p["level"], p["op"])
@@ -428,7 +435,10 @@ def resolved_cycle(cycle, prec):
 
 
 def tail_opt(args):
-    return {} if args.tail_rows is None else {"tail_rows": args.tail_rows}
+    o = {} if args.tail_rows is None else {"tail_rows": args.tail_rows}
+    if args.tail_cluster is not None:
+        o["tail_cluster"] = args.tail_cluster
+    return o
 
 
 def run_case(args):

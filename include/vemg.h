@@ -113,9 +113,12 @@ typedef struct vemg_options {
                          cycle (SA on A_bar); VL_SOR needs Neumann (VEMG_EINVAL otherwise) */
     int cycle;        /* VEMG_CYCLE_*: same arithmetic, different launch structure */
     int tail_rows;    /* per-phase cycles: the first level below the finest with at most this many
-                         rows, and every level under it, run as one single-CTA kernel (0: never);
-                         0..65536, default 0 (measured slower than one kernel per phase once the
-                         kernels load their operator rows before waiting on their predecessor) */
+                         rows, and every level under it, run as one kernel (the coarse tail of the
+                         V-cycle; 0: never); 0..262144 */
+    int tail_cluster; /* the kernel of the coarse tail: 0 = one CTA whose steps are separated by
+                         CTA barriers (tail_rows at most 65536), 2..16 = one thread-block cluster
+                         of that many CTAs whose steps are separated by the hardware cluster
+                         barrier; the vectors stay in global memory either way */
 } vemg_options;
 
 typedef struct vemg_info {
@@ -130,7 +133,7 @@ typedef struct vemg_hierarchy vemg_hierarchy;
 
 /* Fill opts with the paper's parameters (section 6): strength 0.01, omega_p = 2/3, Neumann,
    FP64, coarse_max = 512, max_levels = 10, the additive preconditioner, VEMG_CYCLE_AUTO,
-   tail_rows = 0. */
+   tail_rows = 0, tail_cluster = 0. */
 void vemg_default_options(vemg_options *opts);
 
 /* Assemble the P1 stiffness matrix A_ij = integral grad N_i . grad N_j in physical coordinates
@@ -326,6 +329,7 @@ int vemg_kernel_launches(const vemg_hierarchy *h, int64_t *count);
 #define VEMG_PROBE_TRANSFER 6    /* restrictions, prolongations and E~^T r (sliced-ELL transfers) */
 #define VEMG_PROBE_VECTOR 7      /* the Krylov vector kernels: x/r update, z combination, p update */
 #define VEMG_PROBE_DENSE 8       /* the dense coarsest-level solves */
+#define VEMG_PROBE_TAIL 9        /* the coarse-tail kernels (vemg_options.tail_rows) */
 
 /* Start timing one kernel class (VEMG_PROBE_NONE stops): every later launch of that class
    records a CUDA event before and after itself on its stream. Resets the accumulated totals. */
@@ -342,9 +346,11 @@ int vemg_probe_read(vemg_hierarchy *h, double *total_ms, int64_t *launches, doub
    of the outer residual, 5 dense coarsest solve), its multigrid level, its CTA group (0 surface,
    1 A_bar; a single chain has group 0 only) and the SM clock cycles from the end of the previous
    phase's barrier to the end of its own, seen by the group's first CTA (the phase's critical
-   path). capacity: entries the caller's arrays hold; *count receives the number of phases
-   (VEMG_EINVAL, with *count set, if capacity is smaller; 0 phases without a persistent program).
-   Synchronises the device. */
+   path). Without a persistent program, the same for the steps of the cluster tails
+   (vemg_options.tail_cluster) since vemg_probe(h, VEMG_PROBE_TAIL), timed by the cluster's first
+   CTA (group 0 the surface chain's tail, 1 the A_bar chain's). capacity: entries the caller's arrays hold; *count
+   receives the number of phases (VEMG_EINVAL, with *count set, if capacity is smaller; 0 phases
+   without a persistent program or cluster tail). Synchronises the device. */
 int vemg_probe_phases(vemg_hierarchy *h, int capacity, int *count, int *op, int *level, int *group,
                       double *cycles);
 

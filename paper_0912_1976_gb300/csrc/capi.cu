@@ -119,6 +119,7 @@ void vemg_default_options(vemg_options *o) {
     o->precond = VEMG_PRECOND_ADDITIVE;
     o->cycle = VEMG_CYCLE_AUTO;
     o->tail_rows = 0;
+    o->tail_cluster = 0;
 }
 
 const char *vemg_last_error(void) { return last_cuda_error(); }
@@ -259,7 +260,8 @@ int vemg_setup(const vemg_csr *A, const vemg_mesh *mesh, const vemg_options *opt
             (o.precision != VEMG_PREC_FP64 && o.precision != VEMG_PREC_FP32 && o.precision != VEMG_PREC_BF16) ||
             !(o.strength >= 0.0) ||
             !(o.omega_p > 0.0) || o.coarse_max < 1 || o.coarse_max > 1024 || o.max_levels < 1 ||
-            o.tail_rows < 0 || o.tail_rows > 65536 ||
+            o.tail_rows < 0 || o.tail_rows > (o.tail_cluster > 0 ? 262144 : 65536) || o.tail_cluster < 0 ||
+            o.tail_cluster == 1 || o.tail_cluster > 16 ||
             o.max_levels > kMaxLevels || o.precond < VEMG_PRECOND_ADDITIVE || o.precond > VEMG_PRECOND_NONE ||
             (o.precond == VEMG_PRECOND_VL_SOR && o.bc != VEMG_NEUMANN) ||
             (o.cycle != VEMG_CYCLE_PERSISTENT && o.cycle != VEMG_CYCLE_LAUNCHES && o.cycle != VEMG_CYCLE_AUTO &&
@@ -303,6 +305,8 @@ void vemg_destroy(vemg_hierarchy *h) {
     release_graphs(h);
     release_batch(h);
     release_persist(h);
+    release_ctail(h->ssurf);
+    release_ctail(h->sbar);
     for (auto &e : h->probe.ev) cudaEventDestroy(e);
     h->arena.release();
     delete h;
@@ -447,9 +451,13 @@ int vemg_kernel_launches(const vemg_hierarchy *h, int64_t *count) {
 
 int vemg_probe(vemg_hierarchy *h, int kind) {
     return guarded([&] {
-        if (!h || kind < VEMG_PROBE_NONE || kind > VEMG_PROBE_DENSE) return VEMG_EINVAL;
+        if (!h || kind < VEMG_PROBE_NONE || kind > VEMG_PROBE_TAIL) return VEMG_EINVAL;
         probe_start(h, kind);
         if (kind == VEMG_PROBE_VCYCLE) persist_profile_reset(h);
+        if (kind == VEMG_PROBE_TAIL) {
+            ctail_profile_reset(h->ssurf);
+            ctail_profile_reset(h->sbar);
+        }
         return VEMG_OK;
     });
 }
@@ -459,7 +467,22 @@ int vemg_probe_phases(vemg_hierarchy *h, int capacity, int *count, int *op, int 
     return guarded([&] {
         if (!h || !count || capacity < 0 || (capacity > 0 && (!op || !level || !group || !cycles)))
             return VEMG_EINVAL;
-        return persist_profile(h, capacity, count, op, level, group, cycles);
+        if (h->persist || !(h->ssurf.ctail || h->sbar.ctail))
+            return persist_profile(h, capacity, count, op, level, group, cycles);
+        // the cluster tails: the surface chain's as group 0, the A_bar chain's as group 1
+        std::vector<int> o, l, g;
+        std::vector<double> c;
+        ctail_profile(h->ssurf, 0, o, l, g, c);
+        ctail_profile(h->sbar, 1, o, l, g, c);
+        *count = (int)o.size();
+        if (capacity < *count) return VEMG_EINVAL;
+        for (int k = 0; k < *count; ++k) {
+            op[k] = o[k];
+            level[k] = l[k];
+            group[k] = g[k];
+            cycles[k] = c[k];
+        }
+        return VEMG_OK;
     });
 }
 

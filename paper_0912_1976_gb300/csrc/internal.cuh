@@ -38,6 +38,12 @@ void set_last_error_message(const char *msg);   // a library-side reason behind 
 
 inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
 
+// a * b + c rounded once. The solve kernels that must give the same bits for the same row (the
+// per-phase kernels and the cluster tail) spell out every multiply-add with these, so that no
+// difference in the compiler's contraction choices can separate them.
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // ------------------------------------------------------------------------------------------
 // programmatic dependent launch: a kernel launched with pdl_launch may start while the kernel
 // before it on the stream finishes; pdl_begin() at its top waits until that kernel has completed
@@ -139,7 +145,7 @@ struct Level {
 // launch, plus the algorithmic bytes of each launch (bytes the operation must move at minimum).
 enum ProbeKind {
     PROBE_NONE = 0, PROBE_SPMV_A = 1, PROBE_SOR = 2, PROBE_RESIDUAL = 3, PROBE_SOR_FINE = 4, PROBE_VCYCLE = 5,
-    PROBE_TRANSFER = 6, PROBE_VECTOR = 7, PROBE_DENSE = 8
+    PROBE_TRANSFER = 6, PROBE_VECTOR = 7, PROBE_DENSE = 8, PROBE_TAIL = 9
 };
 
 struct Probe {
@@ -192,6 +198,8 @@ struct SChain {
     // the coarse tail (levels tail_level.. as one single-CTA kernel, persist.cu); -1: none
     int tail_level = -1, tail_n = 0;
     const void *tail = nullptr;
+    void *ctail = nullptr;         // the tail as one thread-block cluster (persist.cu), host object
+    double tail_bytes = 0.0;       // algorithmic bytes of one tail launch
 };
 
 struct Chain {
@@ -273,7 +281,12 @@ int barrier_selftest(int claimed, int launched, cudaStream_t s);
 int solve_scalar_iters();   // index of the iteration count among the solve's device scalars
 void persist_profile_reset(vemg_hierarchy *h);
 void build_tails(vemg_hierarchy *h, cudaStream_t s);
-void launch_tail(const SChain &C, cudaStream_t s);
+void launch_tail(const SChain &C, cudaStream_t s, bool profile = false);
+void release_ctail(SChain &C);
+void ctail_profile_reset(SChain &C);
+int ctail_profile(const SChain &C, int group, std::vector<int> &op, std::vector<int> &level, std::vector<int> &grp,
+                  std::vector<double> &cycles);
+double ctail_bytes(const SChain &C);
 int persist_profile(vemg_hierarchy *h, int cap, int *count, int *op, int *level, int *group, double *cycles);
 // setup.cu
 void assemble(const vemg_mesh *mesh, vemg_csr *A_out, cudaStream_t s);

@@ -171,7 +171,7 @@ __device__ __forceinline__ AT prow_from(AT acc, const int *__restrict__ col, con
         }
 #pragma unroll
         for (int u = 0; u < B; ++u)
-            if (k0 + u < w && (lim < 0 || c[u] < lim)) acc += (AT)a[u] * (AT)ldcg(x + c[u]);
+            if (k0 + u < w && (lim < 0 || c[u] < lim)) acc = fmadd((AT)a[u], (AT)ldcg(x + c[u]), acc);
     }
     return acc;
 }
@@ -193,7 +193,7 @@ __device__ __forceinline__ void sell_row_op(const PPhase &p, const double *__res
         if (pre) {
 #pragma unroll
             for (int u = 0; u < kPU; ++u)
-                if (u < w && (lim < 0 || pre->c[u] < lim)) acc += pre->a[u] * ldcg(x + pre->c[u]);
+                if (u < w && (lim < 0 || pre->c[u] < lim)) acc = fmadd(pre->a[u], ldcg(x + pre->c[u]), acc);
             if (w > kPU) acc = prow_from<XT, XT, XT, 8>(acc, p.col, v, o, w, x, lim, kPU);
         } else {
             acc = prow_from<XT, XT, XT, kPU>(acc, p.col, v, o, w, x, lim, 0);
@@ -209,7 +209,7 @@ __device__ __forceinline__ void sell_row_op(const PPhase &p, const double *__res
         case PH_RES: {
             XT d = pre ? pre->d : __ldg((const XT *)p.d + i);
             XT b = pre && p.b_outer ? (XT)pre->bo : rhs<XT>(p, r, i);
-            XT t = d * ldcg((const XT *)p.x + i) + acc;
+            XT t = fmadd(d, ldcg((const XT *)p.x + i), acc);
             stcg((XT *)p.r + i, b - t);
             break;
         }
@@ -259,7 +259,7 @@ __device__ void run_phase(const PPhase &p, const double *__restrict__ r, int gw,
                 }
 #pragma unroll
                 for (int u = 0; u < kPU; ++u)
-                    if (k0 + u < w) acc += a[u] * __ldg(r + c[u]);
+                    if (k0 + u < w) acc = fmadd(a[u], __ldg(r + c[u]), acc);
             }
             stcg(y + m.x + lane, (XT)acc);
         }
@@ -270,7 +270,7 @@ __device__ void run_phase(const PPhase &p, const double *__restrict__ r, int gw,
         XT *x = (XT *)p.x;
         for (int row = gw; row < p.n; row += nw) {
             XT s = 0;
-            for (int k = lane; k < p.n; k += 32) s += __ldg(G + (int64_t)row * p.n + k) * rhs<XT>(p, r, k);
+            for (int k = lane; k < p.n; k += 32) s = fmadd(__ldg(G + (int64_t)row * p.n + k), rhs<XT>(p, r, k), s);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) stcg(x + row, (XT)s);
@@ -354,6 +354,59 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const PPhase *__restri
         run_phase<XT, true>(sp[k], nullptr, gw, nw, lane, pre);
         if (k + 1 < nphases) prefetch<XT>(sp[k + 1], nullptr, gw, lane, pre);
         __syncthreads();   // the phase's writes are visible to the CTA
+    }
+}
+
+// The coarse tail in one thread-block cluster: the program of the single-CTA tail, its steps
+// spread over every warp of the cluster and separated by the hardware cluster barrier (release /
+// acquire at cluster scope) instead of __syncthreads. The vectors stay in global memory and are
+// read and written through L2 (ld.global.cg / st.global.cg), which the barrier orders; remote
+// shared-memory gathers measured slower than L2 hits on this GPU. Each warp loads the operator
+// data of its first row of the next step between arriving at the barrier and waiting on it. The
+// barrier is hardware over CTAs that are co-scheduled by construction: no wait here spins, and
+// every thread of every CTA reaches every barrier.
+static constexpr int kClusterThreads = 512;
+
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
+
+template <class XT>
+__global__ void __launch_bounds__(kClusterThreads, 1) k_tail_cluster(const PPhase *__restrict__ phases, int nphases,
+                                                                      unsigned long long *cycles) {
+    // step descriptors, three deep: the one of step k + 2 is written during step k, so that the
+    // barrier ending step k - 1 has made those of steps k and k + 1 visible to the whole CTA
+    __shared__ PPhase sp[3];
+    unsigned rank;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    // slices go round-robin over the CTAs (slice j of a step to CTA j mod ncta), so that the gathers
+    // of a small step, whose cost is bound by each SM's load pipeline, spread over every SM
+    const int warps = kClusterThreads / 32, lane = threadIdx.x & 31;
+    const int gw = (int)(threadIdx.x >> 5) * (int)gridDim.x + (int)rank, nw = (int)gridDim.x * warps;
+    for (int q = 0; q < 2 && q < nphases; ++q)
+        if (threadIdx.x < kPhaseWords) ((int *)&sp[q])[threadIdx.x] = __ldg((const int *)(phases + q) + threadIdx.x);
+    __syncthreads();
+    Pre<XT> pre;
+    prefetch<XT>(sp[0], nullptr, gw, lane, pre);
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // b of the tail level comes from the previous kernel
+    // profile: CTA 0 times each step up to the end of its barrier (the step's critical path)
+    const bool timer = cycles && rank == 0 && threadIdx.x == 0;
+    long long t0 = timer ? clock64() : 0;
+    for (int k = 0; k < nphases; ++k) {
+        const bool more = k + 1 < nphases;
+        if (k + 2 < nphases && threadIdx.x < kPhaseWords)
+            ((int *)&sp[(k + 2) % 3])[threadIdx.x] = __ldg((const int *)(phases + k + 2) + threadIdx.x);
+        if (!more) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        run_phase<XT, true>(sp[k % 3], nullptr, gw, nw, lane, pre);
+        if (more) {
+            cluster_arrive();
+            prefetch<XT>(sp[(k + 1) % 3], nullptr, gw, lane, pre);
+            cluster_wait();
+        }
+        if (timer) {
+            long long t1 = clock64();
+            atomicAdd(cycles + k, (unsigned long long)(t1 - t0));
+            t0 = t1;
+        }
     }
 }
 
@@ -605,8 +658,37 @@ void build_persist(vemg_hierarchy *h, cudaStream_t s) {
 // colour of such a level has about one row per thread of the tail CTA, so a phase costs one
 // memory round trip plus a CTA barrier instead of a kernel launch; one SM's bandwidth and FP
 // rate bound the size that pays.
-static void build_tail(Arena &ar, SChain &C, bool fp32, int tail_rows, cudaStream_t s) {
+struct ClusterTail {
+    int ncta = 0;
+    unsigned long long *cycles = nullptr;   // device: per step, SM cycles summed over launches
+    std::vector<int> op, level;
+};
+
+template <class XT>
+static bool cluster_schedulable(int ncta) {
+    VEMG_CHECK_CUDA(cudaFuncSetAttribute(k_tail_cluster<XT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ncta);
+    cfg.blockDim = dim3(kClusterThreads);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)ncta;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_tail_cluster<XT>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n >= 1;
+}
+
+// ncta == 0: the single-CTA tail (at most kTailMaxPhases steps); 2..16: one cluster of ncta CTAs
+static void build_tail(Arena &ar, SChain &C, bool fp32, int tail_rows, int ncta, cudaStream_t s) {
     C.tail_level = -1;
+    if (ncta > 0 && !(fp32 ? cluster_schedulable<float>(ncta) : cluster_schedulable<double>(ncta))) return;
     int l0 = -1;
     for (int l = 1; l < C.nlev; ++l)
         if (C.lv[l].n <= tail_rows) {
@@ -616,10 +698,10 @@ static void build_tail(Arena &ar, SChain &C, bool fp32, int tail_rows, cudaStrea
     if (l0 < 0) return;
     Builder B(ar, s);
     B.xs = fp32 ? 4 : 8;
-    for (;;) {   // start deeper while the tail's phases do not fit in the kernel's shared memory
+    for (;;) {   // the single-CTA tail starts deeper while its phases do not fit in shared memory
         B.ph.clear();
         B.vcycle(C, l0, C.lv[l0].b, -1, C.lv[l0].x);
-        if ((int)B.ph.size() <= kTailMaxPhases) break;
+        if (ncta > 0 || (int)B.ph.size() <= kTailMaxPhases) break;
         if (++l0 >= C.nlev) return;
     }
     PPhase *d = ar.alloc<PPhase>((int)B.ph.size());
@@ -627,18 +709,85 @@ static void build_tail(Arena &ar, SChain &C, bool fp32, int tail_rows, cudaStrea
     VEMG_CHECK_CUDA(cudaMemcpy(d, B.ph.data(), sizeof(PPhase) * B.ph.size(), cudaMemcpyHostToDevice));
     C.tail = d;
     C.tail_n = (int)B.ph.size();
+    C.tail_bytes = B.bytes;
     C.tail_level = l0;
+    if (ncta > 0) {
+        auto T = new ClusterTail();
+        T->ncta = ncta;
+        try {
+            T->cycles = ar.alloc<unsigned long long>(C.tail_n);
+            VEMG_CHECK_CUDA(cudaMemset(T->cycles, 0, sizeof(unsigned long long) * C.tail_n));
+        } catch (...) {
+            delete T;
+            throw;
+        }
+        for (const PPhase &p : B.ph) {
+            T->op.push_back(p.op);
+            T->level.push_back(p.level);
+        }
+        C.ctail = T;
+    }
 }
+
+void release_ctail(SChain &C) {
+    delete (ClusterTail *)C.ctail;   // device memory belongs to the hierarchy's arena
+    C.ctail = nullptr;
+}
+
+void ctail_profile_reset(SChain &C) {
+    auto T = (ClusterTail *)C.ctail;
+    if (T) VEMG_CHECK_CUDA(cudaMemset(T->cycles, 0, sizeof(unsigned long long) * C.tail_n));
+}
+
+// the cluster tail's steps with the persistent program's op codes
+int ctail_profile(const SChain &C, int group, std::vector<int> &op, std::vector<int> &level, std::vector<int> &grp,
+                  std::vector<double> &cycles) {
+    auto T = (const ClusterTail *)C.ctail;
+    if (!T) return 0;
+    std::vector<unsigned long long> c(C.tail_n);
+    VEMG_CHECK_CUDA(cudaDeviceSynchronize());
+    VEMG_CHECK_CUDA(cudaMemcpy(c.data(), T->cycles, sizeof(unsigned long long) * c.size(), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < C.tail_n; ++k) {
+        op.push_back(T->op[k]);
+        level.push_back(T->level[k]);
+        grp.push_back(group);
+        cycles.push_back((double)c[k]);
+    }
+    return C.tail_n;
+}
+
+double ctail_bytes(const SChain &C) { return C.tail_bytes; }
 
 void build_tails(vemg_hierarchy *h, cudaStream_t s) {
     const bool fp32 = h->precision != VEMG_PREC_FP64;
     if (h->precond == VEMG_PRECOND_NONE) return;
-    if (!single_chain(h)) build_tail(h->arena, h->ssurf, fp32, h->opts.tail_rows, s);
-    build_tail(h->arena, h->sbar, fp32, h->opts.tail_rows, s);
+    SChain *cs[2] = {single_chain(h) ? nullptr : &h->ssurf, &h->sbar};
+    for (SChain *C : cs)
+        if (C) build_tail(h->arena, *C, fp32, h->opts.tail_rows, h->opts.tail_cluster, s);
 }
 
-void launch_tail(const SChain &C, cudaStream_t s) {
+void launch_tail(const SChain &C, cudaStream_t s, bool profile) {
     const PPhase *ph = (const PPhase *)C.tail;
+    if (C.ctail) {
+        auto T = (const ClusterTail *)C.ctail;
+        unsigned long long *cyc = profile ? T->cycles : nullptr;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)T->ncta);
+        cfg.blockDim = dim3(kClusterThreads);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[2];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)T->ncta;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 2;
+        if (C.fp32) VEMG_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_tail_cluster<float>, ph, C.tail_n, cyc));
+        else VEMG_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_tail_cluster<double>, ph, C.tail_n, cyc));
+        return;
+    }
     if (C.fp32)
         pdl_launch(k_tail<float>, 1, kTailThreads, s, ph, C.tail_n);
     else

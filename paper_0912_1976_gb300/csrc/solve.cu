@@ -143,7 +143,7 @@ __device__ __forceinline__ AT sell_row(const RowHead<VT> &h, const int *__restri
     AT acc = 0;
 #pragma unroll
     for (int u = 0; u < kU; ++u)
-        if (u < w && (lim < 0 || h.c[u] < lim)) acc += (AT)(float_or_self(h.a[u])) * (AT)x[h.c[u]];
+        if (u < w && (lim < 0 || h.c[u] < lim)) acc = fmadd((AT)(float_or_self(h.a[u])), (AT)x[h.c[u]], acc);
     for (int k0 = kU; k0 < w; k0 += kU) {
         int c[kU];
         VT a[kU];
@@ -155,7 +155,7 @@ __device__ __forceinline__ AT sell_row(const RowHead<VT> &h, const int *__restri
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u)
-            if (k0 + u < w && (lim < 0 || c[u] < lim)) acc += (AT)(float_or_self(a[u])) * (AT)x[c[u]];
+            if (k0 + u < w && (lim < 0 || c[u] < lim)) acc = fmadd((AT)(float_or_self(a[u])), (AT)x[c[u]], acc);
     }
     return acc;
 }
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_residual(int nsl, const int
     }
     pdl_begin();
     if (!active) return;
-    XT acc = dg * x[i] + sell_row<VT, XT, XT>(h, col, v, o, w, x, -1);
+    XT acc = fmadd(dg, x[i], sell_row<VT, XT, XT>(h, col, v, o, w, x, -1));
     r[i] = (XT)b[i] - acc;
 }
 
@@ -262,7 +262,7 @@ __global__ void k_dense_mv(int n, const XT *__restrict__ Gm, const BT *__restric
     int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
     if (row >= n) return;
     XT s = 0;
-    for (int k = lane; k < n; k += 32) s += Gm[(int64_t)row * n + k] * (XT)b[k];
+    for (int k = lane; k < n; k += 32) s = fmadd(Gm[(int64_t)row * n + k], (XT)b[k], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) x[row] = (XT)s;
@@ -358,9 +358,10 @@ static void vcycle_level(const SChain &C, int l, const BT *b, XT *x, cudaStream_
     const SLevel &L = C.lv[l];
     const bool fine = C.is_bar && l == 0;
     if (l > 0 && l == C.tail_level) {
-        // the coarse tail: every level from here down and back up in one single-CTA kernel
-        // (its phases read b and write x in this level's own buffers)
-        launch_tail(C, s);
+        // the coarse tail: every level from here down and back up in one kernel (one CTA, or one
+        // thread-block cluster); it reads b and writes x in this level's own buffers
+        ProbeScope ps(PROBE_TAIL, ctail_bytes(C), s);
+        launch_tail(C, s, g_probe && g_probe->kind == PROBE_TAIL);
         SOLVE_LAUNCHED();
         return;
     }
@@ -751,7 +752,7 @@ static void precond_t(vemg_hierarchy *h, const double *r, double *z, int first, 
     // probes of the per-phase kernel classes time the launch-per-phase cycle
     const int pk = h->probe.kind;
     const bool persist = h->persist && pk != PROBE_SOR && pk != PROBE_SOR_FINE && pk != PROBE_RESIDUAL &&
-                         pk != PROBE_TRANSFER && pk != PROBE_DENSE;
+                         pk != PROBE_TRANSFER && pk != PROBE_DENSE && pk != PROBE_TAIL;
     const bool none = h->precond == VEMG_PRECOND_NONE;
     const bool hybrid = persist && persist_coarse_only(h);
     if (none) {

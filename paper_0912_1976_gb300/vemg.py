@@ -37,7 +37,8 @@ class vemg_csr(C.Structure):
 
 class vemg_options(C.Structure):
     _fields_ = [("bc", C.c_int), ("precision", C.c_int), ("strength", C.c_double), ("omega_p", C.c_double),
-                ("coarse_max", C.c_int), ("max_levels", C.c_int), ("precond", C.c_int), ("cycle", C.c_int), ("tail_rows", C.c_int)]
+                ("coarse_max", C.c_int), ("max_levels", C.c_int), ("precond", C.c_int), ("cycle", C.c_int), ("tail_rows", C.c_int),
+                ("tail_cluster", C.c_int)]
 
 
 class vemg_info(C.Structure):
@@ -103,7 +104,7 @@ PROTOTYPES = {
     "vemg_probe_phases": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), _VP, _VP, _VP, _VP]),
 }
 (VEMG_PROBE_NONE, VEMG_PROBE_SPMV_A, VEMG_PROBE_SOR_COARSE, VEMG_PROBE_RESIDUAL, VEMG_PROBE_SOR_FINE, VEMG_PROBE_VCYCLE,
- VEMG_PROBE_TRANSFER, VEMG_PROBE_VECTOR, VEMG_PROBE_DENSE) = range(9)
+ VEMG_PROBE_TRANSFER, VEMG_PROBE_VECTOR, VEMG_PROBE_DENSE, VEMG_PROBE_TAIL) = range(10)
 VEMG_PROBE_SOR = VEMG_PROBE_SOR_COARSE
 
 
