@@ -49,7 +49,12 @@ def lib():
         dp, ip, u8p = C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_uint8)
         L.or_setup.restype = C.c_void_p
         L.or_setup.argtypes = [C.c_int, dp, C.c_int, ip, u8p, C.c_int, ip, C.c_int, C.c_double,
-                               C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, ip]
+                               C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, ip]
+        L.or_tentative_qr.argtypes = [C.c_int, C.c_int, dp, dp, dp]
+        L.or_linear_prolongator.argtypes = [C.c_int, ip, ip, dp, ip, C.c_int, dp, C.c_int, C.c_double, C.c_int,
+                                            ip, ip, dp, dp, C.c_int]
+        L.or_get_nullspace.argtypes = [C.c_void_p, C.c_int, C.c_int, dp]
+        L.or_block_norms.argtypes = [C.c_int, ip, ip, dp, ip, C.c_int, ip, ip, dp, C.c_int]
         L.or_free.argtypes = [C.c_void_p]
         L.or_size.restype = C.c_long
         L.or_size.argtypes = [C.c_void_p, C.c_char_p, C.c_int, C.c_int]
@@ -96,7 +101,7 @@ class Problem:
     """Oracle setup of one mesh: ordering, A, E~, E~^T A E~, and the two SA chains."""
 
     def __init__(self, mesh, bc: int = BC_NEUMANN, theta=THETA, omega_p=OMEGA_P, coarse_max=COARSE_MAX,
-                 max_levels=MAX_LEVELS, natural_order=False, precond=PC_ADDITIVE):
+                 max_levels=MAX_LEVELS, natural_order=False, precond=PC_ADDITIVE, surf_ns=1):
         L = lib()
         self._keep = (_f64(mesh.xyz), _i32(mesh.tets), np.ascontiguousarray(mesh.tags, dtype=np.uint8),
                       _i32(mesh.top_tris))
@@ -104,7 +109,7 @@ class Problem:
         st = C.c_int(0)
         self.h = L.or_setup(xyz.shape[0], _p(xyz, C.c_double), tets.shape[0], _p(tets, C.c_int),
                             _p(tags, C.c_uint8), tris.shape[0], _p(tris, C.c_int), bc, theta, omega_p,
-                            coarse_max, max_levels, int(natural_order), precond, C.byref(st))
+                            coarse_max, max_levels, int(natural_order), precond, surf_ns, C.byref(st))
         if not self.h:
             raise OracleError(f"or_setup failed: {STATUS.get(st.value, st.value)}")
         self.bc = bc
@@ -145,6 +150,15 @@ class Problem:
         rc = lib().or_get_int(self.h, name.encode(), which, level, _p(out, C.c_int))
         if rc:
             raise OracleError(f"no int array {name}")
+        return out
+
+    def nullspace(self, which=0, level=0) -> np.ndarray:
+        """Near-nullspace rows (lev.n x nsd) of a level of a {1, x, y} chain."""
+        nsd = self.size("nsd", which)
+        out = np.zeros((self.size("lev.n", which, level), nsd))
+        rc = lib().or_get_nullspace(self.h, which, level, _p(out, C.c_double))
+        if rc:
+            raise OracleError("no near-nullspace rows")
         return out
 
     def nlev(self, which):
@@ -235,6 +249,53 @@ def smoothed_prolongator(A: sp.csr_matrix, agg, nagg, omega=OMEGA_P, theta=THETA
     if nnz < 0:
         raise OracleError("prolongator capacity")
     return sp.csr_matrix((pv[:nnz], pci[:nnz], prp), shape=(n, int(nagg)))
+
+
+def block_norms(A: sp.csr_matrix, blk, nblk):
+    """Block strength matrix: (I, J) = Frobenius norm of A's block (I, J) (blocks: consecutive rows)."""
+    A = A.tocsr()
+    A.sort_indices()
+    rp, ci, v, bk = _i32(A.indptr), _i32(A.indices), _f64(A.data), _i32(blk)
+    cap = A.nnz + 1
+    srp = np.zeros(nblk + 1, np.int32)
+    sci = np.zeros(cap, np.int32)
+    sv = np.zeros(cap)
+    nnz = lib().or_block_norms(A.shape[0], _p(rp, C.c_int), _p(ci, C.c_int), _p(v, C.c_double), _p(bk, C.c_int),
+                               int(nblk), _p(srp, C.c_int), _p(sci, C.c_int), _p(sv, C.c_double), cap)
+    return sp.csr_matrix((sv[:nnz], sci[:nnz], srp), shape=(nblk, nblk))
+
+
+def tentative_qr(Bj):
+    """Local QR of one aggregate's near-nullspace rows (k x d): (Q k x kept, R kept x d)."""
+    Bj = _f64(Bj)
+    k, d = Bj.shape
+    Q = np.zeros((k, d))
+    R = np.zeros((d, d))
+    kept = lib().or_tentative_qr(k, d, _p(Bj, C.c_double), _p(Q, C.c_double), _p(R, C.c_double))
+    return Q[:, :kept].copy(), R[:kept].copy()
+
+
+def linear_prolongator(A: sp.csr_matrix, agg, nagg, B, omega=OMEGA_P, smoothed=True):
+    """Tentative (smoothed=False) or smoothed prolongator of the {1, x, y} chain for the given
+    aggregates and near-nullspace rows B (n x d); returns (P, coarse near-nullspace rows)."""
+    A = A.tocsr()
+    A.sort_indices()
+    n = A.shape[0]
+    B = _f64(B)
+    d = B.shape[1]
+    rp, ci, v, ag = _i32(A.indptr), _i32(A.indices), _f64(A.data), _i32(agg)
+    cap = (A.nnz + n) * d * 4 + 16
+    prp = np.zeros(n + 1, np.int32)
+    pci = np.zeros(cap, np.int32)
+    pv = np.zeros(cap)
+    Bc = np.zeros((int(nagg) * d, d))
+    nc = lib().or_linear_prolongator(n, _p(rp, C.c_int), _p(ci, C.c_int), _p(v, C.c_double), _p(ag, C.c_int),
+                                     int(nagg), _p(B, C.c_double), d, omega, int(smoothed), _p(prp, C.c_int),
+                                     _p(pci, C.c_int), _p(pv, C.c_double), _p(Bc, C.c_double), cap)
+    if nc < 0:
+        raise OracleError("prolongator capacity")
+    nnz = int(prp[n])
+    return sp.csr_matrix((pv[:nnz], pci[:nnz], prp), shape=(n, nc)), Bc[:nc].copy()
 
 
 def colour(A: sp.csr_matrix):

@@ -278,6 +278,9 @@ typedef struct {
     int *cptr;    /* ncolours + 1 offsets into crow */
     int *crow;    /* rows grouped by colour, ascending within a colour */
     double *x, *b, *r; /* work vectors */
+    double *B;    /* near-nullspace rows (n x nsd, row-major) of a chain with nsd > 1, else NULL */
+    int *blk;     /* node block of each unknown (the aggregate it came from), NULL on level 0 */
+    int nblk;     /* number of node blocks */
 } level;
 
 typedef struct {
@@ -289,6 +292,8 @@ typedef struct {
     double *Lc;        /* dense Cholesky factor, nc x nc row-major lower */
     double sigma;      /* rank-one regularisation added on singular chains */
     int natural;       /* use natural-order (sequential) Gauss-Seidel instead of multicolour */
+    int nsd;           /* near-nullspace vectors: 1 (constants) or 3 ({1, x, y}) */
+    double *nu;        /* nsd > 1: the coarsest level's nullspace vector (the coarse constant) */
 } chain;
 
 /* strength of connection: |A_ij| > theta sqrt(A_ii A_jj), i != j (section 6) */
@@ -609,6 +614,198 @@ int or_smoothed_prolongator(int n, const int *rp, const int *ci, const double *v
     return nnz;
 }
 
+/* ------------------------------------------------------------------------------------------ */
+/* smoothed aggregation with the near-nullspace {1, x, y} (Vanek, Mandel and Brezina 1996, the    */
+/* fourth-order recipe), for the surface operator E~^T A E~ of vertically unstructured meshes    */
+
+/* Block strength matrix of a level whose unknowns come in node blocks (the coarse unknowns of
+   one aggregate): entry (I, J) is the Frobenius norm of the block A_IJ, its squares summed over
+   the rows of block I in ascending order and each row's entries in ascending column order. The
+   rows of a block are consecutive. */
+static csr block_norm_matrix(const csr *A, const int *blk, int nblk) {
+    int n = A->n;
+    int *bptr = (int *)xcalloc((size_t)nblk + 1, sizeof(int));
+    for (int i = 0; i < n; ++i) bptr[blk[i] + 1]++;
+    for (int I = 0; I < nblk; ++I) bptr[I + 1] += bptr[I];
+    int *mark = (int *)xcalloc((size_t)nblk, sizeof(int));
+    for (int J = 0; J < nblk; ++J) mark[J] = -1;
+    int *rp = (int *)xcalloc((size_t)nblk + 1, sizeof(int));
+    for (int I = 0; I < nblk; ++I) {
+        int c = 0;
+        for (int i = bptr[I]; i < bptr[I + 1]; ++i)
+            for (int k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+                int J = blk[A->ci[k]];
+                if (mark[J] != I) { mark[J] = I; c++; }
+            }
+        rp[I + 1] = rp[I] + c;
+    }
+    csr S = csr_new(nblk, nblk, rp[nblk]);
+    memcpy(S.rp, rp, sizeof(int) * ((size_t)nblk + 1));
+    double *acc = (double *)xcalloc((size_t)nblk, sizeof(double));
+    for (int J = 0; J < nblk; ++J) mark[J] = -1;
+    for (int I = 0; I < nblk; ++I) {
+        int base = S.rp[I], c = 0;
+        for (int i = bptr[I]; i < bptr[I + 1]; ++i)
+            for (int k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+                int J = blk[A->ci[k]];
+                if (mark[J] != I) { mark[J] = I; acc[J] = 0.0; S.ci[base + c++] = J; }
+                acc[J] = acc[J] + A->v[k] * A->v[k];
+            }
+        qsort(S.ci + base, (size_t)c, sizeof(int), cmp_int);
+        for (int q = 0; q < c; ++q) S.v[base + q] = sqrt(acc[S.ci[base + q]]);
+    }
+    free(acc); free(mark); free(rp); free(bptr);
+    return S;
+}
+
+/* exported for tests: the block strength matrix (returns its entries, -1 if cap is too small) */
+int or_block_norms(int n, const int *rp, const int *ci, const double *v, const int *blk, int nblk, int *srp,
+                   int *sci, double *sv, int cap) {
+    csr A;
+    A.n = n; A.m = n; A.rp = (int *)rp; A.ci = (int *)ci; A.v = (double *)v;
+    csr S = block_norm_matrix(&A, blk, nblk);
+    int nnz = csr_nnz(&S);
+    if (nnz <= cap) {
+        memcpy(srp, S.rp, sizeof(int) * ((size_t)nblk + 1));
+        memcpy(sci, S.ci, sizeof(int) * (size_t)nnz);
+        memcpy(sv, S.v, sizeof(double) * (size_t)nnz);
+    }
+    csr_del(&S);
+    return nnz <= cap ? nnz : -1;
+}
+
+#define QR_DROP 1e-10   /* a near-nullspace column whose part outside the kept ones is below this
+                           fraction of its norm adds no coarse unknown (e.g. 1 or 2 nodes) */
+
+/* Local QR of one aggregate's near-nullspace rows Bj (k x d, row-major) by modified Gram-Schmidt
+   in column order, every sum in ascending row order: Q (k x d, row-major, kept columns first)
+   with orthonormal columns spanning Bj's columns, and R = Q^T Bj (kept x d, row-major). A column
+   whose residual after the kept ones has norm <= QR_DROP times its own norm is dropped. Returns
+   the number of kept columns. */
+int or_tentative_qr(int k, int d, const double *Bj, double *Q, double *R) {
+    int kept = 0;
+    double *v = (double *)xcalloc((size_t)k, sizeof(double));
+    for (int c = 0; c < d; ++c) {
+        double n0 = 0.0;
+        for (int i = 0; i < k; ++i) { v[i] = Bj[i * d + c]; n0 = n0 + v[i] * v[i]; }
+        n0 = sqrt(n0);
+        for (int a = 0; a < kept; ++a) {
+            double t = 0.0;
+            for (int i = 0; i < k; ++i) t = t + Q[i * d + a] * v[i];
+            for (int i = 0; i < k; ++i) v[i] = v[i] - t * Q[i * d + a];
+        }
+        double nr = 0.0;
+        for (int i = 0; i < k; ++i) nr = nr + v[i] * v[i];
+        nr = sqrt(nr);
+        if (!(nr > QR_DROP * n0)) continue;
+        for (int i = 0; i < k; ++i) Q[i * d + kept] = v[i] / nr;
+        kept++;
+    }
+    for (int a = 0; a < kept; ++a)
+        for (int c = 0; c < d; ++c) {
+            double t = 0.0;
+            for (int i = 0; i < k; ++i) t = t + Q[i * d + a] * Bj[i * d + c];
+            R[a * d + c] = t;
+        }
+    free(v);
+    return kept;
+}
+
+/* Tentative prolongator of aggregates agg (every unknown aggregated) with near-nullspace rows B
+   (n x d): aggregate J's unknowns, ascending, get the rows of its local Q; its kept columns are
+   the coarse unknowns of J, numbered aggregate by aggregate. The coarse near-nullspace rows are
+   the local R's (nc x d), and the coarse unknowns' blocks their aggregates. */
+static csr tentative_linear(int n, const int *agg, int nagg, const double *B, int d, double **Bc_out,
+                            int **blk_out) {
+    int *cnt = (int *)xcalloc((size_t)nagg + 1, sizeof(int));
+    for (int i = 0; i < n; ++i) cnt[agg[i] + 1]++;
+    for (int J = 0; J < nagg; ++J) cnt[J + 1] += cnt[J];
+    int *mem = (int *)xcalloc((size_t)n, sizeof(int)), *cur = (int *)xcalloc((size_t)nagg, sizeof(int));
+    memcpy(cur, cnt, sizeof(int) * (size_t)nagg);
+    for (int i = 0; i < n; ++i) mem[cur[agg[i]]++] = i;   /* ascending within each aggregate */
+    int kmax = 1;
+    for (int J = 0; J < nagg; ++J) if (cnt[J + 1] - cnt[J] > kmax) kmax = cnt[J + 1] - cnt[J];
+    double *Bj = (double *)xcalloc((size_t)kmax * d, sizeof(double)), *Q = (double *)xcalloc((size_t)kmax * d, sizeof(double));
+    double *R = (double *)xcalloc((size_t)nagg * d * d, sizeof(double));
+    int *kept = (int *)xcalloc((size_t)nagg, sizeof(int)), *col0 = (int *)xcalloc((size_t)nagg + 1, sizeof(int));
+    double *qv = (double *)xcalloc((size_t)n * d, sizeof(double));
+    for (int J = 0; J < nagg; ++J) {
+        int k = cnt[J + 1] - cnt[J];
+        for (int t = 0; t < k; ++t)
+            for (int c = 0; c < d; ++c) Bj[t * d + c] = B[(size_t)mem[cnt[J] + t] * d + c];
+        kept[J] = or_tentative_qr(k, d, Bj, Q, R + (size_t)J * d * d);
+        col0[J + 1] = col0[J] + kept[J];
+        for (int t = 0; t < k; ++t)
+            for (int a = 0; a < kept[J]; ++a) qv[(size_t)mem[cnt[J] + t] * d + a] = Q[t * d + a];
+    }
+    int nc = col0[nagg];
+    csr Pt = csr_new(n, nc, 0);
+    free(Pt.ci); free(Pt.v);
+    for (int i = 0; i < n; ++i) Pt.rp[i + 1] = Pt.rp[i] + kept[agg[i]];
+    Pt.ci = (int *)xcalloc((size_t)Pt.rp[n], sizeof(int));
+    Pt.v = (double *)xcalloc((size_t)Pt.rp[n], sizeof(double));
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < kept[agg[i]]; ++a) {
+            Pt.ci[Pt.rp[i] + a] = col0[agg[i]] + a;
+            Pt.v[Pt.rp[i] + a] = qv[(size_t)i * d + a];
+        }
+    double *Bc = (double *)xcalloc((size_t)nc * d, sizeof(double));
+    int *blk = (int *)xcalloc((size_t)nc, sizeof(int));
+    for (int J = 0; J < nagg; ++J)
+        for (int a = 0; a < kept[J]; ++a) {
+            blk[col0[J] + a] = J;
+            for (int c = 0; c < d; ++c) Bc[(size_t)(col0[J] + a) * d + c] = R[(size_t)J * d * d + a * d + c];
+        }
+    free(cnt); free(mem); free(cur); free(Bj); free(Q); free(R); free(kept); free(col0); free(qv);
+    *Bc_out = Bc;
+    *blk_out = blk;
+    return Pt;
+}
+
+/* P = (I - omega D^-1 A) P_t with the unfiltered A and its diagonal D (section 6: omega = 2/3):
+   A P_t by Gustavson's rule, then P_ij = (P_t)_ij - (omega / A_ii) (A P_t)_ij on the pattern of
+   A P_t. (The filtered matrix of the constant chains keeps the constants only; with {1, x, y} the
+   unfiltered matrix keeps the linear functions as well.) */
+static csr smooth_unfiltered(const csr *A, const csr *Pt, double omega) {
+    csr AP = csr_spgemm(A, Pt);
+    for (int i = 0; i < A->n; ++i) {
+        int q = csr_find(A, i, i);
+        double d = q >= 0 ? A->v[q] : 0.0;
+        double w = d > 0.0 ? omega / d : 0.0;
+        for (int k = AP.rp[i]; k < AP.rp[i + 1]; ++k) {
+            int p = csr_find(Pt, i, AP.ci[k]);
+            double pt = p >= 0 ? Pt->v[p] : 0.0;
+            double t = w * AP.v[k];
+            AP.v[k] = pt - t;
+        }
+    }
+    return AP;
+}
+
+/* exported for tests: the tentative and smoothed prolongators of the {1, x, y} chain for given
+   aggregates (every unknown aggregated); Bc receives the coarse near-nullspace rows (nc x d) */
+int or_linear_prolongator(int n, const int *rp, const int *ci, const double *v, const int *agg, int nagg,
+                          const double *B, int d, double omega, int smoothed, int *prp, int *pci, double *pv,
+                          double *Bc, int cap) {
+    csr A;
+    A.n = n; A.m = n; A.rp = (int *)rp; A.ci = (int *)ci; A.v = (double *)v;
+    double *bc = NULL;
+    int *blk = NULL;
+    csr Pt = tentative_linear(n, agg, nagg, B, d, &bc, &blk);
+    csr P = smoothed ? smooth_unfiltered(&A, &Pt, omega) : Pt;
+    int nnz = csr_nnz(&P), nc = P.m;
+    if (nnz <= cap) {
+        memcpy(prp, P.rp, sizeof(int) * ((size_t)n + 1));
+        memcpy(pci, P.ci, sizeof(int) * (size_t)nnz);
+        memcpy(pv, P.v, sizeof(double) * (size_t)nnz);
+        memcpy(Bc, bc, sizeof(double) * (size_t)nc * d);
+    }
+    if (smoothed) csr_del(&P);
+    csr_del(&Pt);
+    free(bc); free(blk);
+    return nnz <= cap ? nc : -1;
+}
+
 static void level_colour(level *L) {
     int n = L->A.n;
     L->colour = (int *)xcalloc((size_t)n, sizeof(int));
@@ -639,7 +836,15 @@ static int chain_factor_coarsest(chain *C) {
             if (L->A.ci[k] == i) tr += L->A.v[k];
         }
     C->sigma = 0.0;
-    if (C->singular) {
+    if (C->singular && C->nu) {
+        /* nullspace nu (the coarse constant of a {1, x, y} chain): A + sigma nu nu^T with
+           sigma nu^T nu = tr(A) / n */
+        double nn = 0.0;
+        for (int i = 0; i < n; ++i) nn = nn + C->nu[i] * C->nu[i];
+        C->sigma = tr / ((double)n * nn);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) a[(size_t)i * n + j] += C->sigma * C->nu[i] * C->nu[j];
+    } else if (C->singular) {
         C->sigma = tr / ((double)n * (double)n);
         for (size_t k = 0; k < (size_t)n * n; ++k) a[k] += C->sigma;
     }
@@ -659,18 +864,53 @@ static int chain_factor_coarsest(chain *C) {
     return OR_OK;
 }
 
+/* B0: near-nullspace rows of level 0 (n x nsd) for nsd > 1 (owned by the chain afterwards) */
 static int chain_build(chain *C, csr A0, int singular, double theta, double omega_p, int coarse_max,
-                       int max_levels, int natural) {
+                       int max_levels, int natural, int nsd, double *B0) {
     memset(C, 0, sizeof(*C));
     C->singular = singular;
     C->natural = natural;
+    C->nsd = nsd;
     if (max_levels > MAX_LEVELS_CAP) max_levels = MAX_LEVELS_CAP;
     if (max_levels < 1) max_levels = 1;
     C->lv[0].A = A0;
+    C->lv[0].B = B0;
+    C->lv[0].nblk = A0.n;
     C->nlev = 1;
     while (C->nlev < max_levels && C->lv[C->nlev - 1].A.n > coarse_max) {
         level *L = &C->lv[C->nlev - 1];
         int n = L->A.n;
+        if (nsd > 1) {
+            /* aggregates of node blocks, by the block strength (level 0: the unknowns themselves) */
+            int nb = L->nblk;
+            int *bagg = (int *)xcalloc((size_t)nb, sizeof(int));
+            int nagg;
+            if (L->blk) {
+                csr S = block_norm_matrix(&L->A, L->blk, nb);
+                nagg = or_sa_aggregate(nb, S.rp, S.ci, S.v, theta, singular, bagg);
+                csr_del(&S);
+            } else {
+                nagg = or_sa_aggregate(n, L->A.rp, L->A.ci, L->A.v, theta, singular, bagg);
+            }
+            int *agg = (int *)xcalloc((size_t)n, sizeof(int));
+            for (int i = 0; i < n; ++i) agg[i] = bagg[L->blk ? L->blk[i] : i];
+            free(bagg);
+            double *Bc = NULL;
+            int *blk = NULL;
+            csr Pt = tentative_linear(n, agg, nagg, L->B, nsd, &Bc, &blk);
+            if (nagg == 0 || (long)Pt.m * 10 > (long)n * 9) { csr_del(&Pt); free(Bc); free(blk); free(agg); break; }
+            L->agg = agg;
+            L->P = smooth_unfiltered(&L->A, &Pt, omega_p);
+            csr_del(&Pt);
+            L->PT = csr_transpose(&L->P);
+            level *Nx = &C->lv[C->nlev];
+            Nx->A = galerkin(&L->A, &L->P, &L->PT);
+            Nx->B = Bc;
+            Nx->blk = blk;
+            Nx->nblk = nagg;
+            C->nlev++;
+            continue;
+        }
         int *agg = (int *)xcalloc((size_t)n, sizeof(int));
         int nagg = or_sa_aggregate(n, L->A.rp, L->A.ci, L->A.v, theta, singular, agg);
         if (nagg == 0 || (long)nagg * 10 > (long)n * 9) { free(agg); break; }
@@ -680,6 +920,12 @@ static int chain_build(chain *C, csr A0, int singular, double theta, double omeg
         level *Nx = &C->lv[C->nlev];
         Nx->A = galerkin(&L->A, &L->P, &L->PT);
         C->nlev++;
+    }
+    if (nsd > 1 && singular) {
+        /* the coarsest level's nullspace: the first near-nullspace column (the coarse constant) */
+        level *Lc = &C->lv[C->nlev - 1];
+        C->nu = (double *)xcalloc((size_t)Lc->A.n, sizeof(double));
+        for (int i = 0; i < Lc->A.n; ++i) C->nu[i] = Lc->B[(size_t)i * nsd];
     }
     for (int l = 0; l < C->nlev; ++l) level_colour(&C->lv[l]);
     C->direct = C->lv[C->nlev - 1].A.n <= coarse_max;
@@ -693,8 +939,9 @@ static void chain_free(chain *C) {
         csr_del(&L->A); csr_del(&L->P); csr_del(&L->PT);
         free(L->agg); free(L->colour); free(L->cptr); free(L->crow);
         free(L->x); free(L->b); free(L->r);
+        free(L->B); free(L->blk);
     }
-    free(C->Lc);
+    free(C->Lc); free(C->nu);
     memset(C, 0, sizeof(*C));
 }
 
@@ -730,10 +977,18 @@ static void coarse_solve(const chain *C, const level *L, const double *b, double
         return;
     }
     const double *a = C->Lc;
-    double mu = 0.0;
-    if (C->singular) mu = vsum(n, b) / (double)n;
+    const double *nu = C->nu;
+    double mu = 0.0, nn = 0.0;
+    if (C->singular && nu) {
+        /* project the right-hand side on the complement of the nullspace nu */
+        double t = 0.0;
+        for (int i = 0; i < n; ++i) { t = t + nu[i] * b[i]; nn = nn + nu[i] * nu[i]; }
+        mu = t / nn;
+    } else if (C->singular) {
+        mu = vsum(n, b) / (double)n;
+    }
     for (int i = 0; i < n; ++i) {
-        double s = b[i] - mu;
+        double s = b[i] - (nu ? mu * nu[i] : mu);
         for (int k = 0; k < i; ++k) s -= a[(size_t)i * n + k] * x[k];
         x[i] = s / a[(size_t)i * n + i];
     }
@@ -742,7 +997,12 @@ static void coarse_solve(const chain *C, const level *L, const double *b, double
         for (int k = i + 1; k < n; ++k) s -= a[(size_t)k * n + i] * x[k];
         x[i] = s / a[(size_t)i * n + i];
     }
-    if (C->singular) {
+    if (C->singular && nu) {
+        double t = 0.0;
+        for (int i = 0; i < n; ++i) t = t + nu[i] * x[i];
+        double m2 = t / nn;
+        for (int i = 0; i < n; ++i) x[i] -= m2 * nu[i];
+    } else if (C->singular) {
         double m2 = vsum(n, x) / (double)n;
         for (int i = 0; i < n; ++i) x[i] -= m2;
     }
@@ -1059,12 +1319,17 @@ static csr csr_copy(const csr *a) {
 
 void or_free(void *hp);
 
+/* surf_ns: near-nullspace of the surface chain's smoothed aggregation, 1 (constants) or 3
+   ({1, x, y} with the top nodes' horizontal coordinates) */
 void *or_setup(int n, const double *xyz, int ntet, const int *tets, const unsigned char *tags, int ntri,
                const int *tris, int bc, double theta, double omega_p, int coarse_max, int max_levels,
-               int natural_order, int precond, int *status) {
+               int natural_order, int precond, int surf_ns, int *status) {
     *status = OR_OK;
     if (n <= 0 || ntet <= 0 || (bc != BC_NEUMANN && bc != BC_DIRICHLET_TOP) || precond < PC_ADDITIVE ||
-        precond > PC_NONE || (precond == PC_VL_SOR && bc != BC_NEUMANN)) { *status = OR_EINVAL; return NULL; }
+        precond > PC_NONE || (precond == PC_VL_SOR && bc != BC_NEUMANN) || (surf_ns != 1 && surf_ns != 3)) {
+        *status = OR_EINVAL;
+        return NULL;
+    }
     for (int e = 0; e < 4 * ntet; ++e) if (tets[e] < 0 || tets[e] >= n) { *status = OR_EMESH; return NULL; }
     problem *h = (problem *)xcalloc(1, sizeof(problem));
     h->n = n; h->bc = bc; h->ntet = ntet;
@@ -1083,13 +1348,25 @@ void *or_setup(int n, const double *xyz, int ntet, const int *tets, const unsign
         rc = build_extrapolation(h, ntri, tris, tags);
         if (rc) { csr_del(&Abar); or_free(h); *status = rc; return NULL; }
         h->Ac = galerkin(&h->A, &h->E, &h->ET);
-        rc = chain_build(&h->surf, csr_copy(&h->Ac), 1, theta, omega_p, coarse_max, max_levels, natural_order);
+        double *B0 = NULL;
+        if (surf_ns == 3) {
+            /* {1, x, y} at the top nodes (internal rows 0 .. mtop-1) */
+            B0 = (double *)xcalloc((size_t)h->mtop * 3, sizeof(double));
+            for (int r = 0; r < h->mtop; ++r) {
+                const double *p = h->xyz + 3 * h->new2old[r];
+                B0[3 * r] = 1.0;
+                B0[3 * r + 1] = p[0];
+                B0[3 * r + 2] = p[1];
+            }
+        }
+        rc = chain_build(&h->surf, csr_copy(&h->Ac), 1, theta, omega_p, coarse_max, max_levels, natural_order,
+                         surf_ns, B0);
         if (rc) { csr_del(&Abar); or_free(h); *status = rc; return NULL; }
     }
-    rc = chain_build(&h->bar, Abar, 0, theta, omega_p, coarse_max, max_levels, natural_order);
+    rc = chain_build(&h->bar, Abar, 0, theta, omega_p, coarse_max, max_levels, natural_order, 1, NULL);
     if (rc) { or_free(h); *status = rc; return NULL; }
     if (h->precond == PC_SA) {
-        rc = chain_build(&h->one, csr_copy(&h->A), 1, theta, omega_p, coarse_max, max_levels, natural_order);
+        rc = chain_build(&h->one, csr_copy(&h->A), 1, theta, omega_p, coarse_max, max_levels, natural_order, 1, NULL);
         if (rc) { or_free(h); *status = rc; return NULL; }
     } else if (h->precond == PC_VL_SOR) {
         /* level 0: A with the vertical extrapolation E~ as its prolongator; below it, the SA chain
@@ -1106,6 +1383,7 @@ void *or_setup(int n, const double *xyz, int ntet, const int *tets, const unsign
         V->lv[0].PT = csr_copy(&h->ET);
         for (int l = 0; l < S->nlev; ++l) V->lv[l + 1] = S->lv[l];
         V->direct = S->direct; V->nc = S->nc; V->Lc = S->Lc; V->sigma = S->sigma;
+        V->nsd = S->nsd; V->nu = S->nu;
         memset(S, 0, sizeof(*S));
         level_colour(&V->lv[0]);
     }
@@ -1263,6 +1541,7 @@ long or_size(void *hp, const char *key, int which, int l) {
     if (!strcmp(key, "nnzAc")) return h->Ac.rp ? csr_nnz(&h->Ac) : 0;
     if (!strcmp(key, "nlev")) return C->nlev;
     if (!strcmp(key, "direct")) return C->direct;
+    if (!strcmp(key, "nsd")) return C->nsd;
     if (l < 0 || l >= C->nlev) return -1;
     if (!strcmp(key, "lev.n")) return C->lv[l].A.n;
     if (!strcmp(key, "lev.nnz")) return csr_nnz(&C->lv[l].A);
@@ -1310,6 +1589,15 @@ int or_get_int(void *hp, const char *name, int which, int l, int *out) {
     }
     if (!strcmp(name, "lev.colour")) { memcpy(out, C->lv[l].colour, sizeof(int) * (size_t)C->lv[l].A.n); return OR_OK; }
     return OR_EINVAL;
+}
+
+/* the near-nullspace rows of a level of a {1, x, y} chain (lev.n x nsd, row-major) */
+int or_get_nullspace(void *hp, int which, int l, double *out) {
+    problem *h = (problem *)hp;
+    const chain *C = pick_chain(h, which);
+    if (l < 0 || l >= C->nlev || !C->lv[l].B) return OR_EINVAL;
+    memcpy(out, C->lv[l].B, sizeof(double) * (size_t)C->lv[l].A.n * C->nsd);
+    return OR_OK;
 }
 
 /* one V-cycle of a chain on its finest level (for tests of the cycle alone) */

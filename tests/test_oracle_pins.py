@@ -939,3 +939,144 @@ def test_bf16_rounded_cycle_symmetric_positive_and_near_fp64(pc):
     rel = np.linalg.norm(V16 - V64) / np.linalg.norm(V64)
     assert 1e-3 < rel < 2e-2, rel
     assert np.linalg.norm(M16 - M64) <= 2e-2 * np.linalg.norm(M64)
+
+
+# --------------------------------------------------------------------------------------------
+# smoothed aggregation with the near-nullspace {1, x, y} (surface chain of unstructured meshes)
+
+def test_tentative_qr_orthonormal_reconstructs_and_drops_dependent_columns():
+    """Local QR of an aggregate's near-nullspace rows: orthonormal Q, Q R = B, R upper triangular,
+    the same column space as a textbook QR (numpy), and dependent columns dropped: one node keeps
+    the constant only, two nodes keep two columns, collinear and coincident nodes lose theirs."""
+    rng = np.random.default_rng(5)
+    for k in (3, 5, 12, 40):
+        xy = 0.5 + 0.01 * rng.standard_normal((k, 2))
+        B = np.column_stack([np.ones(k), xy])
+        Q, R = O.tentative_qr(B)
+        assert Q.shape == (k, 3)
+        assert np.abs(Q.T @ Q - np.eye(3)).max() <= 1e-12
+        assert np.abs(Q @ R - B).max() <= 1e-13
+        assert np.abs(np.tril(R, -1)).max() <= 1e-12 * np.abs(B).max()
+        Qn, _ = np.linalg.qr(B)
+        assert np.abs(Q @ Q.T - Qn @ Qn.T).max() <= 1e-10
+    assert O.tentative_qr(np.array([[1.0, 0.3, 0.7]]))[0].shape == (1, 1)
+    assert O.tentative_qr(np.array([[1.0, 0.3, 0.7], [1.0, 0.4, 0.2]]))[0].shape == (2, 2)
+    t = np.array([0.1, 0.2, 0.35, 0.5])
+    collinear = np.column_stack([np.ones(4), t, 2.0 * t + 1.0])
+    assert O.tentative_qr(collinear)[0].shape == (4, 2)
+    coincident = np.tile([1.0, 0.3, 0.7], (3, 1))
+    assert O.tentative_qr(coincident)[0].shape == (3, 1)
+
+
+def test_block_strength_is_the_frobenius_norm_of_each_block():
+    """The strength of the coarse levels of the {1, x, y} chain is measured between node blocks:
+    entry (I, J) is the Frobenius norm of the block A_IJ (numpy's norm of the dense block)."""
+    rng = np.random.default_rng(9)
+    sizes = [3, 2, 3, 1, 3]
+    blk = np.repeat(np.arange(len(sizes)), sizes)
+    n = blk.size
+    M = rng.standard_normal((n, n)) * (rng.random((n, n)) < 0.5)
+    M = M + M.T
+    S = O.block_norms(sp.csr_matrix(M), blk, len(sizes)).toarray()
+    for I in range(len(sizes)):
+        for J in range(len(sizes)):
+            blkIJ = M[np.ix_(blk == I, blk == J)]
+            assert abs(S[I, J] - np.linalg.norm(blkIJ)) <= 1e-14 * max(1.0, np.linalg.norm(blkIJ))
+
+
+def test_linear_prolongator_reproduces_linear_functions_on_a_path():
+    """Path of 9 nodes at x_i = i h, [-1, 2, -1] with Neumann ends, aggregates of three, near-nullspace
+    {1, x}: the tentative prolongator has orthonormal columns and reproduces 1 and x exactly
+    (P_t B_c = B). The 1D Laplacian annihilates linear functions at interior rows, so the smoothed P
+    (omega = 2/3, D^-1 of the unfiltered A) still reproduces them there; at the left end
+    (A x)_0 = x_0 - x_1 = -h and D_00 = 1, so (P B_c)_0 = (1, 0 + (2/3) h) by hand."""
+    n, h = 9, 0.125
+    A = _lap1d(n).tolil()
+    A[0, 0] = A[n - 1, n - 1] = 1.0
+    A = A.tocsr()
+    x = h * np.arange(n)
+    B = np.column_stack([np.ones(n), x])
+    agg = np.repeat(np.arange(3), 3)
+    Pt, Bc = O.linear_prolongator(A, agg, 3, B, smoothed=False)
+    assert Pt.shape == (n, 6) and Bc.shape == (6, 2)
+    assert np.abs((Pt.T @ Pt).toarray() - np.eye(6)).max() <= 1e-14
+    assert np.abs(Pt @ Bc - B).max() <= 1e-14
+    P, Bc2 = O.linear_prolongator(A, agg, 3, B)
+    assert np.array_equal(Bc, Bc2)
+    PB = P @ Bc
+    assert np.abs(PB[1:n - 1] - B[1:n - 1]).max() <= 1e-14
+    assert np.abs(PB[0] - [1.0, (2.0 / 3.0) * h]).max() <= 1e-15
+    assert np.abs(PB[n - 1] - [1.0, x[n - 1] - (2.0 / 3.0) * h]).max() <= 1e-15
+
+
+def _xy_mesh(nx, nz, eps, seed=8):
+    return I.make_mesh(nx, nx, nz, I.depth_sines(eps), z_jitter=0.3, xy_jitter=0.2, seed=seed)
+
+
+def test_linear_chain_invariants():
+    """On an xy-jittered mesh (surface chain of three levels or more): every coarse level has at most three
+    unknowns per aggregate; its near-nullspace rows are reproduced by the smoothed prolongator as
+    (I - omega D^-1 A) applied to the fine ones; the coarse constant (first near-nullspace column)
+    is prolonged to the fine constant and spans the kernel of every coarse operator; the coarse
+    operators are exactly symmetric Galerkin products."""
+    m = _xy_mesh(32, 12, 1e-4)
+    P = O.Problem(m, surf_ns=3, coarse_max=40)
+    assert P.size("nsd", 0) == 3 and P.nlev(0) >= 3
+    for l in range(P.nlev(0) - 1):
+        A = P.csr("lev.A", 0, l)
+        Pl = P.csr("lev.P", 0, l)
+        Ac = P.csr("lev.A", 0, l + 1).toarray()
+        Bf, Bc = P.nullspace(0, l), P.nullspace(0, l + 1)
+        nagg = len(set(P.ints("lev.agg", 0, l).tolist()))
+        assert nagg <= Bc.shape[0] <= 3 * nagg
+        D = A.diagonal()
+        ref = Bf - (2.0 / 3.0) * (A @ Bf) / D[:, None]
+        assert np.abs(Pl @ Bc - ref).max() <= 1e-10 * np.abs(Bf).max()
+        # (A B_f[:, 0] vanishes only to rounding, amplified by D^-1 of these eps = 1e-4 levels)
+        assert np.abs(Pl @ Bc[:, 0] - Bf[:, 0]).max() <= 1e-9 * np.abs(Bf[:, 0]).max()
+        assert np.array_equal(Ac, Ac.T)
+        refA = (Pl.T @ (A @ Pl)).toarray()
+        assert np.abs(Ac - refA).max() <= 1e-12 * np.abs(refA).max()
+        assert np.abs(Ac @ Bc[:, 0]).max() <= 1e-10 * np.abs(Ac).max() * np.abs(Bc[:, 0]).max()
+    # level 0 holds {1, x, y} of the top nodes in the internal order
+    n2o = P.ints("new2old")
+    B0 = P.nullspace(0, 0)
+    assert np.array_equal(B0[:, 1:], m.xyz[n2o[:P.mtop], :2]) and np.all(B0[:, 0] == 1.0)
+
+
+def test_linear_chain_preconditioner_symmetric_positive_and_solves():
+    m = _xy_mesh(9, 4, 1e-3, seed=4)
+    P = O.Problem(m, surf_ns=3, coarse_max=20)
+    assert P.nlev(0) >= 2
+    n = P.n
+    Mz = np.stack([P.precond(e) for e in np.eye(n)], axis=1)
+    assert np.abs(Mz - Mz.T).max() <= 1e-10 * np.abs(Mz).max()
+    w = np.linalg.eigvalsh(0.5 * (Mz + Mz.T))
+    assert w[0] > -1e-10 * w[-1]
+    b = I.normal_loads(n, 4)
+    r = P.solve(b, tol=1e-11, maxit=2000)
+    assert r["status"] == "OK"
+    n2o = P.ints("new2old")
+    A = P.csr("A").toarray()
+    bi = b[n2o] - b.mean()
+    K = np.block([[A, np.ones((n, 1))], [np.ones((1, n)), np.zeros((1, 1))]])
+    xs = np.linalg.solve(K, np.concatenate([bi, [0.0]]))[:n]
+    assert np.linalg.norm(r["x"][n2o] - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
+def test_section62_linear_nullspace_gives_eps_independent_rate_on_unstructured_mesh():
+    """Section 6.2: on unstructured meshes the vertically lumped preconditioner converges at a rate
+    independent of eps for small eps. On a 24x24x24 xy-jittered mesh (surface chain of three levels)
+    the constants-only surface chain does not (iterations x1.8 from eps = 1e-2 to 1e-4); with
+    {1, x, y} the counts stay within 10% over eps in {1e-2, 1e-3, 1e-4}."""
+    it = {1: [], 3: []}
+    for eps in (1e-2, 1e-3, 1e-4):
+        m = _xy_mesh(24, 24, eps)
+        for ns in (1, 3):
+            P = O.Problem(m, surf_ns=ns)
+            r = P.solve(I.normal_loads(P.n, 12), tol=1e-8, maxit=3000)
+            assert r["status"] == "OK"
+            it[ns].append(r["iters"])
+    assert max(it[3]) <= 1.1 * min(it[3]), it
+    assert it[1][-1] >= 1.8 * it[1][0], it
+    assert it[3][-1] * 3 <= it[1][-1], it
