@@ -72,6 +72,10 @@ def parse():
     ap.add_argument("--tail-rows", type=int, default=None,
                     help="levels of at most this many rows (below the finest) run as one single-CTA kernel; "
                          "default: the library's")
+    ap.add_argument("--surf-nullspace", type=int, default=None, choices=[1, 3],
+                    help="near-nullspace of the surface chain: 1 (constants) or 3 ({1, x, y}); default: 3 on "
+                         "xy-jittered workloads, else 1")
+    ap.add_argument("--bc", default="neumann", choices=["neumann", "dirichlet_top"])
     ap.add_argument("--tail-cluster", type=int, default=None,
                     help="CTAs of the thread-block cluster that runs the coarse tail (0: one CTA); default: the "
                          "library's")
@@ -235,10 +239,13 @@ def workload_config(args, n):
     kr = args.rhs or w.get("nrhs", 1)
     return {"workload": f"{args.workload}: {w['nx']}x{w['ny']}x{w['nz']} extruded hex->6 tets, {n} nodes, "
                         f"H0 {w['depth'][1]:g}, z-jitter {w['z_jitter']}, xy-jitter {w['xy_jitter']}, "
-                        f"all-Neumann, N(0,1) loads mean-zero, rtol {RTOL:g}",
+                        f"{'all-Neumann' if args.bc == 'neumann' else 'Dirichlet top'}, N(0,1) loads"
+                        f"{' mean-zero' if args.bc == 'neumann' else ''}, rtol {RTOL:g}",
             "precision": args.precision, "preconditioner": args.precond, "cycle": args.cycle, "rhs_per_step": kr,
             "tail_rows": args.tail_rows if args.tail_rows is not None else "default",
             "tail_cluster": args.tail_cluster if args.tail_cluster is not None else "default",
+            "surface_nullspace": {1: "constants", 3: "{1, x, y}"}[surf_ns(args)],
+            "bc": args.bc,
             "l2": "inputs larger than L2 (A alone 0.39 GB; no flush needed)",
             "parallelism": f"independent problems x{args.gpus}" if args.gpus > 1 else "single GPU"}
 
@@ -434,10 +441,19 @@ def resolved_cycle(cycle, prec):
     return cycle
 
 
+def surf_ns(args):
+    if args.surf_nullspace is not None:
+        return args.surf_nullspace
+    from paper_0912_1976_gb300 import inputs as I
+    return 3 if I.WORKLOADS.get(args.workload, {}).get("xy_jitter", 0.0) > 0.0 else 1
+
+
 def tail_opt(args):
     o = {} if args.tail_rows is None else {"tail_rows": args.tail_rows}
     if args.tail_cluster is not None:
         o["tail_cluster"] = args.tail_cluster
+    o["surf_nullspace"] = surf_ns(args)
+    o["bc"] = 0 if args.bc == "neumann" else 1
     return o
 
 

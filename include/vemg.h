@@ -75,7 +75,8 @@ extern "C" {
                               P^T of every level) rounded to BF16 (from FP32, nearest even) and
                               stored in BF16; diagonals, vectors and sums FP32. The cycle runs one
                               kernel per phase; the batched solves and the single-CTA coarse tail
-                              read FP32 copies of the same rounded values */
+                              read FP32 copies of the same rounded values. A surface chain with the
+                              near-nullspace {1, x, y} (surf_nullspace = 3) keeps FP32 values */
 
 /* Tetrahedral mesh, HOST pointers (section 2.1, section 3).
    xyz: n_nodes x 3 doubles (x, y, z), z up, top surface at the largest z of each column.
@@ -115,6 +116,12 @@ typedef struct vemg_options {
     int tail_rows;    /* per-phase cycles: the first level below the finest with at most this many
                          rows, and every level under it, run as one kernel (the coarse tail of the
                          V-cycle; 0: never); 0..262144 */
+    int surf_nullspace; /* near-nullspace of the surface chain's smoothed aggregation: 1 = the
+                         constants (the paper's SA), 3 = {1, x, y} with the top nodes' horizontal
+                         coordinates (Vanek, Mandel and Brezina's choice for fourth-order-like
+                         operators: E~^T A E~ of vertically unstructured meshes, section 4; node
+                         blocks of up to 3 coarse unknowns per aggregate below level 0, strength
+                         by block Frobenius norms, prolongator smoothing with the unfiltered A) */
     int tail_cluster; /* the kernel of the coarse tail: 0 = one CTA whose steps are separated by
                          CTA barriers (tail_rows at most 65536), 2..16 = one thread-block cluster
                          of that many CTAs whose steps are separated by the hardware cluster
@@ -133,7 +140,7 @@ typedef struct vemg_hierarchy vemg_hierarchy;
 
 /* Fill opts with the paper's parameters (section 6): strength 0.01, omega_p = 2/3, Neumann,
    FP64, coarse_max = 512, max_levels = 10, the additive preconditioner, VEMG_CYCLE_AUTO,
-   tail_rows = 0, tail_cluster = 0. */
+   tail_rows = 0, surf_nullspace = 1, tail_cluster = 0. */
 void vemg_default_options(vemg_options *opts);
 
 /* Assemble the P1 stiffness matrix A_ij = integral grad N_i . grad N_j in physical coordinates
@@ -271,8 +278,9 @@ int vemg_selftest_barrier(int claimed_blocks, int launched_blocks, void *stream)
    ---- */
 
 /* Sizes: key is one of "n", "mtop", "nnzA", "nnzE", "nnzAc", "nlev" (of the chain), "direct"
-   (coarsest level of the chain solved by the dense solve), "lev.n", "lev.nnz", "lev.nnzP",
-   "lev.ncolours" (of level `level` of the chain). *out = -1 if the item does not exist. */
+   (coarsest level of the chain solved by the dense solve), "nsd" (near-nullspace vectors of the
+   chain: 1 or 3), "lev.n", "lev.nnz", "lev.nnzP", "lev.ncolours" (of level `level` of the
+   chain). *out = -1 if the item does not exist. */
 int vemg_get_size(const vemg_hierarchy *h, const char *key, int chain, int level, int64_t *out);
 
 /* Copy a CSR matrix to HOST arrays sized by vemg_get_size: name is "A" (internal order), "E"
@@ -284,6 +292,12 @@ int vemg_get_csr(const vemg_hierarchy *h, const char *name, int chain, int level
    located top triangle of each internal node, -1 on top nodes), "lev.agg" (aggregate of each
    node of a level), "lev.colour" (colour of each node of a level). */
 int vemg_get_int(const vemg_hierarchy *h, const char *name, int chain, int level, int32_t *out_host);
+
+/* Copy the near-nullspace rows of a level of a chain built with the near-nullspace {1, x, y}
+   (vemg_options.surf_nullspace = 3) to HOST: lev.n x 3 doubles, row-major; level 0 holds
+   (1, x, y) of the top nodes, a coarser level the rows R of its aggregates' local QR
+   factorisations. VEMG_EINVAL for a chain with the constant near-nullspace. */
+int vemg_get_nullspace(const vemg_hierarchy *h, int chain, int level, double *out_host);
 
 /* y = A x on the unknowns of the hierarchy's boundary condition (internal order, device). */
 int vemg_spmv(vemg_hierarchy *h, const double *x_dev, double *y_dev, void *stream);

@@ -1638,12 +1638,14 @@ static void round_offdiag_bf16(csr *a, int keep_diagonal) {
 /* the operators of every level of every chain, as the BF16 variant of the cycle stores them:
    off-diagonal entries of each level matrix and every entry of P and P^T rounded to BF16; the
    diagonal and the dense coarsest factor keep their FP64 values (the setup is unchanged, only
-   the stored operators of the cycle are rounded) */
+   the stored operators of the cycle are rounded). A chain with the near-nullspace {1, x, y} keeps
+   its values (the BF16 variant stores that chain in FP32: BF16 loses the fourth-order-like part
+   of its coarse operators). */
 void or_round_operators_bf16(void *hp) {
     problem *h = (problem *)hp;
     chain *cs[3] = {&h->surf, &h->bar, &h->one};
     for (int c = 0; c < 3; ++c)
-        for (int l = 0; l < cs[c]->nlev; ++l) {
+        for (int l = 0; l < cs[c]->nlev && cs[c]->nsd <= 1; ++l) {
             level *L = &cs[c]->lv[l];
             round_offdiag_bf16(&L->A, 1);
             if (l + 1 < cs[c]->nlev) {

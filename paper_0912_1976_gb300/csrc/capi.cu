@@ -119,6 +119,7 @@ void vemg_default_options(vemg_options *o) {
     o->precond = VEMG_PRECOND_ADDITIVE;
     o->cycle = VEMG_CYCLE_AUTO;
     o->tail_rows = 0;
+    o->surf_nullspace = 1;
     o->tail_cluster = 0;
 }
 
@@ -261,7 +262,7 @@ int vemg_setup(const vemg_csr *A, const vemg_mesh *mesh, const vemg_options *opt
             !(o.strength >= 0.0) ||
             !(o.omega_p > 0.0) || o.coarse_max < 1 || o.coarse_max > 1024 || o.max_levels < 1 ||
             o.tail_rows < 0 || o.tail_rows > (o.tail_cluster > 0 ? 262144 : 65536) || o.tail_cluster < 0 ||
-            o.tail_cluster == 1 || o.tail_cluster > 16 ||
+            o.tail_cluster == 1 || o.tail_cluster > 16 || (o.surf_nullspace != 1 && o.surf_nullspace != 3) ||
             o.max_levels > kMaxLevels || o.precond < VEMG_PRECOND_ADDITIVE || o.precond > VEMG_PRECOND_NONE ||
             (o.precond == VEMG_PRECOND_VL_SOR && o.bc != VEMG_NEUMANN) ||
             (o.cycle != VEMG_CYCLE_PERSISTENT && o.cycle != VEMG_CYCLE_LAUNCHES && o.cycle != VEMG_CYCLE_AUTO &&
@@ -365,6 +366,7 @@ int vemg_get_size(const vemg_hierarchy *h, const char *key, int chain, int level
     else if (!strcmp(key, "nnzAc")) *out = h->Ac.nnz;
     else if (C && !strcmp(key, "nlev")) *out = C->nlev;
     else if (C && !strcmp(key, "direct")) *out = C->direct;
+    else if (C && !strcmp(key, "nsd")) *out = C->nsd;
     else if (C && level >= 0 && level < C->nlev) {
         const Level &L = C->lv[level];
         if (!strcmp(key, "lev.n")) *out = L.A.n;
@@ -373,6 +375,17 @@ int vemg_get_size(const vemg_hierarchy *h, const char *key, int chain, int level
         else if (!strcmp(key, "lev.ncolours")) *out = L.ncolours;
     }
     return VEMG_OK;
+}
+
+int vemg_get_nullspace(const vemg_hierarchy *h, int chain, int level, double *out) {
+    return guarded([&] {
+        const Chain *C = h ? chain_of(h, chain) : nullptr;
+        if (!C || !out || level < 0 || level >= C->nlev || !C->lv[level].B) return VEMG_EINVAL;
+        VEMG_CHECK_CUDA(cudaDeviceSynchronize());
+        VEMG_CHECK_CUDA(cudaMemcpy(out, C->lv[level].B, sizeof(double) * 3 * (size_t)C->lv[level].A.n,
+                                   cudaMemcpyDeviceToHost));
+        return VEMG_OK;
+    });
 }
 
 int vemg_get_csr(const vemg_hierarchy *h, const char *name, int chain, int level, int32_t *rp, int32_t *ci,

@@ -139,6 +139,11 @@ struct Level {
     // FP32 mirrors for the mixed-precision cycle
     float *Af = nullptr, *Pf = nullptr, *PTf = nullptr, *diagf = nullptr;
     float *xf = nullptr, *bf = nullptr, *rf = nullptr;
+    // chains with the near-nullspace {1, x, y}: its rows (n x 3) and, below level 0, the node
+    // blocks (the coarse unknowns of one aggregate, consecutive rows bptr[J] .. bptr[J + 1])
+    double *B = nullptr;
+    int *blk = nullptr, *bptr = nullptr;
+    int nblk = 0;
 };
 
 // Opt-in timing of one kernel class: CUDA events recorded on the launching stream around each
@@ -210,6 +215,8 @@ struct Chain {
     int nc = 0;
     double *G = nullptr;    // nc x nc: inverse of the coarsest operator (projected on singular chains)
     bool is_bar = false;    // the A_bar chain (its level 0 is the finest smoother level)
+    int nsd = 1;            // near-nullspace vectors: 1 (constants) or 3 ({1, x, y})
+    double *nu = nullptr;   // nsd > 1, singular: the coarsest level's nullspace (the coarse constant)
 };
 
 struct Graphs;

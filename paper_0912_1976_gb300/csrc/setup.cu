@@ -1102,6 +1102,261 @@ __global__ void k_prolong_fill(int n, const int *__restrict__ rp, const int *__r
 }
 
 // ------------------------------------------------------------------------------------------
+// smoothed aggregation with the near-nullspace {1, x, y} (the surface chain of vertically
+// unstructured meshes; Vanek, Mandel and Brezina's recipe for fourth-order-like operators). Every
+// step takes the oracle's operations in the oracle's order.
+
+static constexpr int kNsd = 3;
+static constexpr double kQrDrop = 1e-10;   // relative residual norm below which a column is dropped
+
+// block strength matrix: entry (I, J) = Frobenius norm of the block A_IJ, squares summed over the
+// block's rows in ascending order and each row's entries in ascending column order
+__global__ void k_block_norm_len(int nblk, const int *__restrict__ bptr, const int *__restrict__ rp,
+                                 const int *__restrict__ ci, const int *__restrict__ blk, int *len, int *err) {
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nblk) return;
+    int u[kMaxRowUnique];
+    int c = 0;
+    for (int i = bptr[I]; i < bptr[I + 1]; ++i)
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            c = insert_unique(u, c, kMaxRowUnique, blk[ci[k]]);
+            if (c < 0) { atomic_flag(err, VEMG_EINTERNAL); return; }
+        }
+    len[I] = c;
+}
+
+__global__ void k_block_norm_fill(int nblk, const int *__restrict__ bptr, const int *__restrict__ rp,
+                                  const int *__restrict__ ci, const double *__restrict__ v,
+                                  const int *__restrict__ blk, const int *__restrict__ srp, int *sci, double *sv) {
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nblk) return;
+    const int lo = srp[I], hi = srp[I + 1];
+    int c = 0;
+    for (int i = bptr[I]; i < bptr[I + 1]; ++i)
+        for (int k = rp[i]; k < rp[i + 1]; ++k) c = insert_unique(sci + lo, c, hi - lo, blk[ci[k]]);
+    for (int q = lo; q < hi; ++q) sv[q] = 0.0;
+    for (int i = bptr[I]; i < bptr[I + 1]; ++i)
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            int q = bsearch_row(sci, lo, hi, blk[ci[k]]);
+            sv[q] = sv[q] + v[k] * v[k];
+        }
+    for (int q = lo; q < hi; ++q) sv[q] = sqrt(sv[q]);
+}
+
+__global__ void k_map_blocks(int n, const int *__restrict__ blk, const int *__restrict__ bagg, int *agg) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) agg[i] = bagg[blk ? blk[i] : i];
+}
+
+__global__ void k_member_fill(int n, const int *__restrict__ agg, const int *__restrict__ mptr, int *cur, int *mem) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) mem[mptr[agg[i]] + atomicAdd(cur + agg[i], 1)] = i;
+}
+
+// Local QR of each aggregate's near-nullspace rows (members ascending) by modified Gram-Schmidt in
+// column order; one thread per aggregate. qv: rows of Q per unknown (n x 3), vt: a column being
+// orthogonalised (n), R: Q^T B per aggregate (3 x 3), kept: columns kept per aggregate.
+__global__ void k_tentative_qr(int nagg, const int *__restrict__ mptr, const int *__restrict__ mem,
+                               const double *__restrict__ B, double *vt, double *qv, double *R, int *kept) {
+    int J = blockIdx.x * blockDim.x + threadIdx.x;
+    if (J >= nagg) return;
+    const int lo = mptr[J], hi = mptr[J + 1];
+    int kc = 0;
+    for (int c = 0; c < kNsd; ++c) {
+        double n0 = 0.0;
+        for (int t = lo; t < hi; ++t) {
+            int i = mem[t];
+            double v = B[(int64_t)i * kNsd + c];
+            vt[i] = v;
+            n0 = n0 + v * v;
+        }
+        n0 = sqrt(n0);
+        for (int a = 0; a < kc; ++a) {
+            double s = 0.0;
+            for (int t = lo; t < hi; ++t) {
+                int i = mem[t];
+                s = s + qv[(int64_t)i * kNsd + a] * vt[i];
+            }
+            for (int t = lo; t < hi; ++t) {
+                int i = mem[t];
+                vt[i] = vt[i] - s * qv[(int64_t)i * kNsd + a];
+            }
+        }
+        double nr = 0.0;
+        for (int t = lo; t < hi; ++t) nr = nr + vt[mem[t]] * vt[mem[t]];
+        nr = sqrt(nr);
+        if (!(nr > kQrDrop * n0)) continue;
+        for (int t = lo; t < hi; ++t) {
+            int i = mem[t];
+            qv[(int64_t)i * kNsd + kc] = vt[i] / nr;
+        }
+        kc++;
+    }
+    for (int a = 0; a < kc; ++a)
+        for (int c = 0; c < kNsd; ++c) {
+            double s = 0.0;
+            for (int t = lo; t < hi; ++t) {
+                int i = mem[t];
+                s = s + qv[(int64_t)i * kNsd + a] * B[(int64_t)i * kNsd + c];
+            }
+            R[(int64_t)J * kNsd * kNsd + a * kNsd + c] = s;
+        }
+    kept[J] = kc;
+}
+
+__global__ void k_pt_len(int n, const int *__restrict__ agg, const int *__restrict__ kept, int *len) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) len[i] = kept[agg[i]];
+}
+
+__global__ void k_pt_fill(int n, const int *__restrict__ agg, const int *__restrict__ kept,
+                          const int64_t *__restrict__ col0, const int *__restrict__ prp,
+                          const double *__restrict__ qv, int *pci, double *pv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int J = agg[i];
+    for (int a = 0; a < kept[J]; ++a) {
+        pci[prp[i] + a] = (int)col0[J] + a;
+        pv[prp[i] + a] = qv[(int64_t)i * kNsd + a];
+    }
+}
+
+// coarse near-nullspace rows (the local R's) and node blocks of the coarse unknowns
+__global__ void k_coarse_ns(int nagg, const int *__restrict__ kept, const int64_t *__restrict__ col0,
+                            const double *__restrict__ R, double *Bc, int *blk, int *bptr) {
+    int J = blockIdx.x * blockDim.x + threadIdx.x;
+    if (J >= nagg) return;
+    for (int a = 0; a < kept[J]; ++a) {
+        const int64_t r = col0[J] + a;
+        blk[r] = J;
+        for (int c = 0; c < kNsd; ++c) Bc[r * kNsd + c] = R[(int64_t)J * kNsd * kNsd + a * kNsd + c];
+    }
+    bptr[J + 1] = (int)col0[J + 1];
+    if (J == 0) bptr[0] = 0;
+}
+
+// P = P_t - (omega / A_ii) (A P_t) on the pattern of A P_t (AP holds A P_t and becomes P)
+__global__ void k_smooth_unfiltered(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                    const double *__restrict__ v, const int *__restrict__ trp,
+                                    const int *__restrict__ tci, const double *__restrict__ tv,
+                                    const int *__restrict__ arp, const int *__restrict__ aci, double *av,
+                                    double omega) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int q = bsearch_row(ci, rp[i], rp[i + 1], i);
+    double d = q >= 0 ? v[q] : 0.0;
+    double w = d > 0.0 ? omega / d : 0.0;
+    for (int k = arp[i]; k < arp[i + 1]; ++k) {
+        int p = bsearch_row(tci, trp[i], trp[i + 1], aci[k]);
+        double pt = p >= 0 ? tv[p] : 0.0;
+        double t = w * av[k];
+        av[k] = pt - t;
+    }
+}
+
+__global__ void k_column0(int n, const double *__restrict__ B, double *nu) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) nu[i] = B[(int64_t)i * kNsd];
+}
+
+static DCsr csr_spgemm(Arena &ar, const DCsr &L, const DCsr &R, cudaStream_t s);
+
+// One coarsening step of a {1, x, y} chain (singular: every unknown aggregated). Fills L.agg, L.P
+// and the next level's B, blk, bptr, nblk; returns the number of coarse unknowns (0: the
+// coarsening stops here).
+static int coarsen_linear(Arena &ar, Level &L, Level &N, double theta, double omega, cudaStream_t s) {
+    const int n = L.A.n;
+    Arena tmp;
+    int nagg = 0;
+    int *bagg = nullptr;
+    Scratch<int> err(1);
+    VEMG_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    if (L.blk) {
+        const int nb = L.nblk;
+        Scratch<int> len(nb);
+        k_block_norm_len<<<grid_for(nb, 128), 128, 0, s>>>(nb, L.bptr, L.A.rp, L.A.ci, L.blk, len, err);
+        VEMG_CHECK_LAUNCH();
+        if (int e = read_flag(err, s)) throw Error{e};
+        DCsr S;
+        S.n = S.m = nb;
+        S.rp = tmp.alloc<int>(nb + 1);
+        S.nnz = scan_offsets(len, S.rp, nb, s);
+        S.ci = tmp.alloc<int>(S.nnz);
+        S.v = tmp.alloc<double>(S.nnz);
+        k_block_norm_fill<<<grid_for(nb, 128), 128, 0, s>>>(nb, L.bptr, L.A.rp, L.A.ci, L.A.v, L.blk, S.rp, S.ci, S.v);
+        VEMG_CHECK_LAUNCH();
+        Scratch<double> dS(nb);
+        k_diag<<<grid_for(nb, 256), 256, 0, s>>>(nb, S.rp, S.ci, S.v, dS);
+        VEMG_CHECK_LAUNCH();
+        nagg = sa_aggregate(tmp, S, dS, theta, true, &bagg, s);
+    } else {
+        Scratch<double> d(n);
+        k_diag<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, L.A.v, d);
+        VEMG_CHECK_LAUNCH();
+        nagg = sa_aggregate(tmp, L.A, d, theta, true, &bagg, s);
+    }
+    if (nagg == 0) {
+        tmp.release();
+        return 0;
+    }
+    int *agg = ar.alloc<int>(n);
+    k_map_blocks<<<grid_for(n, 256), 256, 0, s>>>(n, L.blk, bagg, agg);
+    VEMG_CHECK_LAUNCH();
+    // members of each aggregate, ascending
+    Scratch<int> cnt(nagg + 1), mptr(nagg + 1), cur(nagg), mem(n);
+    VEMG_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (nagg + 1), s));
+    VEMG_CHECK_CUDA(cudaMemsetAsync(cur, 0, sizeof(int) * nagg, s));
+    k_count_cols<<<grid_for(n, 256), 256, 0, s>>>(agg, n, cnt);
+    VEMG_CHECK_LAUNCH();
+    scan_offsets(cnt, mptr, nagg, s);
+    k_member_fill<<<grid_for(n, 256), 256, 0, s>>>(n, agg, mptr, cur, mem);
+    VEMG_CHECK_LAUNCH();
+    k_sort_segments<<<grid_for(nagg, 128), 128, 0, s>>>(mptr, mem, nagg);
+    VEMG_CHECK_LAUNCH();
+    // local QR, tentative prolongator, coarse near-nullspace
+    Scratch<double> vt(n), qv((int64_t)n * kNsd), R((int64_t)nagg * kNsd * kNsd);
+    Scratch<int> kept(nagg);
+    k_tentative_qr<<<grid_for(nagg, 64), 64, 0, s>>>(nagg, mptr, mem, L.B, vt, qv, R, kept);
+    VEMG_CHECK_LAUNCH();
+    Scratch<int64_t> col0(nagg + 1);
+    const int64_t nc64 = scan_to64(kept, col0, nagg, s);
+    if (nc64 == 0 || nc64 * 10 > (int64_t)n * 9) {
+        tmp.release();
+        return 0;
+    }
+    const int nc = (int)nc64;
+    DCsr Pt;
+    Pt.n = n;
+    Pt.m = nc;
+    {
+        Scratch<int> plen(n);
+        k_pt_len<<<grid_for(n, 256), 256, 0, s>>>(n, agg, kept, plen);
+        VEMG_CHECK_LAUNCH();
+        Pt.rp = tmp.alloc<int>(n + 1);
+        Pt.nnz = scan_offsets(plen, Pt.rp, n, s);
+        Pt.ci = tmp.alloc<int>(Pt.nnz);
+        Pt.v = tmp.alloc<double>(Pt.nnz);
+        k_pt_fill<<<grid_for(n, 256), 256, 0, s>>>(n, agg, kept, col0, Pt.rp, qv, Pt.ci, Pt.v);
+        VEMG_CHECK_LAUNCH();
+    }
+    N.B = ar.alloc<double>((int64_t)nc * kNsd);
+    N.blk = ar.alloc<int>(nc);
+    N.bptr = ar.alloc<int>(nagg + 1);
+    N.nblk = nagg;
+    k_coarse_ns<<<grid_for(nagg, 128), 128, 0, s>>>(nagg, kept, col0, R, N.B, N.blk, N.bptr);
+    VEMG_CHECK_LAUNCH();
+    // P = (I - omega D^-1 A) P_t with the unfiltered A
+    L.P = csr_spgemm(ar, L.A, Pt, s);
+    k_smooth_unfiltered<<<grid_for(n, 128), 128, 0, s>>>(n, L.A.rp, L.A.ci, L.A.v, Pt.rp, Pt.ci, Pt.v, L.P.rp,
+                                                         L.P.ci, L.P.v, omega);
+    VEMG_CHECK_LAUNCH();
+    L.agg = agg;
+    VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+    tmp.release();
+    return nc;
+}
+
+// ------------------------------------------------------------------------------------------
 // SOR colouring: greedy first-fit in round-synchronous smallest-last order
 //
 // Peeling: round t sets the threshold k_t = max(k_{t-1}, smallest remaining degree), k_{-1} = 0,
@@ -1408,6 +1663,40 @@ __global__ void k_trace(int n, const int *__restrict__ rp, const int *__restrict
     *out = s;
 }
 
+// D += sigma nu nu^T (the rank-one regularisation of a singular chain with nullspace nu)
+__global__ void k_dense_rank1(int n, double *D, double sigma, const double *__restrict__ nu) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x) {
+        int i = t / n, j = t % n;
+        D[t] += sigma * nu[i] * nu[j];
+    }
+}
+
+// G := Q G Q, Q = I - nu nu^T / (nu^T nu) (G symmetric); one block
+__global__ void k_project_dense_nu(int n, double *G, const double *__restrict__ nu) {
+    __shared__ double gnu[1024];
+    __shared__ double nn, nugnu;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) s += G[(int64_t)i * n + j] * nu[j];
+        gnu[i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < n; ++i) {
+            a += nu[i] * nu[i];
+            b += nu[i] * gnu[i];
+        }
+        nn = a;
+        nugnu = b;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+        int i = t / n, j = t % n;
+        G[t] = G[t] - (gnu[i] * nu[j] + nu[i] * gnu[j]) / nn + nu[i] * nu[j] * nugnu / (nn * nn);
+    }
+}
+
 static void coarse_inverse(Arena &ar, Chain &C, cudaStream_t s) {
     Level &L = C.lv[C.nlev - 1];
     int n = L.A.n;
@@ -1421,19 +1710,35 @@ static void coarse_inverse(Arena &ar, Chain &C, cudaStream_t s) {
         double t = 0.0;
         VEMG_CHECK_CUDA(cudaMemcpyAsync(&t, tr.p, sizeof(double), cudaMemcpyDeviceToHost, s));
         VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
-        sigma = t / ((double)n * (double)n);
+        if (C.nu) {
+            // sigma nu^T nu = tr(A) / n
+            std::vector<double> hnu(n);
+            VEMG_CHECK_CUDA(cudaMemcpy(hnu.data(), C.nu, sizeof(double) * n, cudaMemcpyDeviceToHost));
+            double nn = 0.0;
+            for (int i = 0; i < n; ++i) nn = nn + hnu[i] * hnu[i];
+            sigma = t / ((double)n * nn);
+        } else {
+            sigma = t / ((double)n * (double)n);
+        }
     }
     Scratch<double> D((int64_t)n * n);
     Scratch<int> err(1);
     VEMG_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     k_dense_fill<<<n, 128, 0, s>>>(n, L.A.rp, L.A.ci, L.A.v, D);
     VEMG_CHECK_LAUNCH();
-    k_dense_cholesky<<<1, 1024, 0, s>>>(n, D, sigma, err);
+    if (C.nu) {
+        k_dense_rank1<<<grid_for((int64_t)n * n, 256), 256, 0, s>>>(n, D, sigma, C.nu);
+        VEMG_CHECK_LAUNCH();
+    }
+    k_dense_cholesky<<<1, 1024, 0, s>>>(n, D, C.nu ? 0.0 : sigma, err);
     VEMG_CHECK_LAUNCH();
     C.G = ar.alloc<double>((int64_t)n * n);
     k_dense_inverse_cols<<<grid_for(n, 64), 64, 0, s>>>(n, D, C.G);
     VEMG_CHECK_LAUNCH();
-    if (C.singular) {
+    if (C.singular && C.nu) {
+        k_project_dense_nu<<<1, 1024, 0, s>>>(n, C.G, C.nu);
+        VEMG_CHECK_LAUNCH();
+    } else if (C.singular) {
         k_project_dense<<<1, 1024, 0, s>>>(n, C.G);
         VEMG_CHECK_LAUNCH();
     }
@@ -1443,6 +1748,15 @@ static void coarse_inverse(Arena &ar, Chain &C, cudaStream_t s) {
 // ------------------------------------------------------------------------------------------
 // chains
 
+__global__ void k_top_nullspace(int mtop, const int *__restrict__ new2old, const double *__restrict__ xyz, double *B) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= mtop) return;
+    const double *p = xyz + 3 * (int64_t)new2old[r];
+    B[(int64_t)r * kNsd] = 1.0;
+    B[(int64_t)r * kNsd + 1] = p[0];
+    B[(int64_t)r * kNsd + 2] = p[1];
+}
+
 static DCsr copy_csr(Arena &ar, const DCsr &a, cudaStream_t s) {
     DCsr c = csr_alloc(ar, a.n, a.m, a.nnz);
     VEMG_CHECK_CUDA(cudaMemcpyAsync(c.rp, a.rp, sizeof(int) * (a.n + 1), cudaMemcpyDeviceToDevice, s));
@@ -1451,14 +1765,27 @@ static DCsr copy_csr(Arena &ar, const DCsr &a, cudaStream_t s) {
     return c;
 }
 
-static void build_chain(Arena &ar, Chain &C, DCsr A0, bool singular, const vemg_options &o, cudaStream_t s) {
+// B0: near-nullspace rows of level 0 (n x 3) for a {1, x, y} chain, else null
+static void build_chain(Arena &ar, Chain &C, DCsr A0, bool singular, const vemg_options &o, cudaStream_t s,
+                        double *B0 = nullptr) {
     C.singular = singular;
     C.nlev = 1;
     C.lv[0].A = A0;
+    C.nsd = B0 ? kNsd : 1;
+    C.lv[0].B = B0;
+    C.lv[0].nblk = A0.n;
     int max_levels = std::min(std::max(o.max_levels, 1), kMaxLevels);
     while (C.nlev < max_levels && C.lv[C.nlev - 1].A.n > o.coarse_max) {
         Level &L = C.lv[C.nlev - 1];
         int n = L.A.n;
+        if (C.nsd > 1) {
+            Level &N = C.lv[C.nlev];
+            if (coarsen_linear(ar, L, N, o.strength, o.omega_p, s) == 0) break;
+            L.PT = csr_transpose(ar, L.P, s);
+            N.A = galerkin(ar, L.A, L.P, L.PT, s);
+            C.nlev++;
+            continue;
+        }
         Scratch<double> d(n);
         k_diag<<<grid_for(n, 256), 256, 0, s>>>(n, L.A.rp, L.A.ci, L.A.v, d);
         VEMG_CHECK_LAUNCH();
@@ -1501,6 +1828,13 @@ static void build_chain(Arena &ar, Chain &C, DCsr A0, bool singular, const vemg_
         L.r = ar.alloc<double>(L.A.n);
     }
     C.direct = C.lv[C.nlev - 1].A.n <= o.coarse_max;
+    if (C.nsd > 1 && singular) {
+        // the coarsest level's nullspace: its first near-nullspace column (the coarse constant)
+        const Level &Lc = C.lv[C.nlev - 1];
+        C.nu = ar.alloc<double>(Lc.A.n);
+        k_column0<<<grid_for(Lc.A.n, 256), 256, 0, s>>>(Lc.A.n, Lc.B, C.nu);
+        VEMG_CHECK_LAUNCH();
+    }
     if (C.direct) coarse_inverse(ar, C, s);
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
 }
@@ -1619,7 +1953,14 @@ void setup(vemg_hierarchy *h, const vemg_csr *Ain, const vemg_mesh *mesh, cudaSt
         VEMG_CHECK_LAUNCH();
         h->ET = csr_transpose(ar, E, s);
         h->Ac = galerkin(ar, h->A, h->E, h->ET, s);
-        build_chain(ar, h->surf, copy_csr(ar, h->Ac, s), true, h->opts, s);
+        double *B0 = nullptr;
+        if (h->opts.surf_nullspace == 3) {
+            // {1, x, y} at the top nodes (internal rows 0 .. mtop - 1)
+            B0 = ar.alloc<double>((int64_t)h->mtop * kNsd);
+            k_top_nullspace<<<grid_for(h->mtop, 256), 256, 0, s>>>(h->mtop, h->new2old, xyz, B0);
+            VEMG_CHECK_LAUNCH();
+        }
+        build_chain(ar, h->surf, copy_csr(ar, h->Ac, s), true, h->opts, s, B0);
     }
     h->bar.is_bar = true;
     build_chain(ar, h->bar, Abar, false, h->opts, s);
@@ -1640,6 +1981,8 @@ void setup(vemg_hierarchy *h, const vemg_csr *Ain, const vemg_mesh *mesh, cudaSt
         V.direct = S.direct;
         V.nc = S.nc;
         V.G = S.G;
+        V.nsd = S.nsd;
+        V.nu = S.nu;
         Level &L = V.lv[0];
         colour_level(ar, L, s);
         L.diag = ar.alloc<double>(L.A.n);

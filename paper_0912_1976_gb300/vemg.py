@@ -38,7 +38,7 @@ class vemg_csr(C.Structure):
 class vemg_options(C.Structure):
     _fields_ = [("bc", C.c_int), ("precision", C.c_int), ("strength", C.c_double), ("omega_p", C.c_double),
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("precond", C.c_int), ("cycle", C.c_int), ("tail_rows", C.c_int),
-                ("tail_cluster", C.c_int)]
+                ("surf_nullspace", C.c_int), ("tail_cluster", C.c_int)]
 
 
 class vemg_info(C.Structure):
@@ -85,6 +85,7 @@ PROTOTYPES = {
     "vemg_get_size": (C.c_int, [_VP, C.c_char_p, C.c_int, C.c_int, C.POINTER(C.c_int64)]),
     "vemg_get_csr": (C.c_int, [_VP, C.c_char_p, C.c_int, C.c_int, _VP, _VP, _VP]),
     "vemg_get_int": (C.c_int, [_VP, C.c_char_p, C.c_int, C.c_int, _VP]),
+    "vemg_get_nullspace": (C.c_int, [_VP, C.c_int, C.c_int, _VP]),
     "vemg_spmv": (C.c_int, [_VP, _DP, _DP, _VP]),
     "vemg_precond": (C.c_int, [_VP, _DP, _DP, _VP]),
     "vemg_vcycle": (C.c_int, [_VP, C.c_int, _DP, _DP, _VP]),
@@ -366,6 +367,14 @@ def vemg_get_int(h: Hierarchy, name: str, chain=1, level=0) -> np.ndarray:
     out = np.zeros(max(cnt, 1), np.int32)
     _check(lib().vemg_get_int(h.h, name.encode(), chain, level, C.c_void_p(out.ctypes.data)),
            f"vemg_get_int({name})")
+    return out[:cnt]
+
+
+def vemg_get_nullspace(h: Hierarchy, chain=0, level=0) -> np.ndarray:
+    """Near-nullspace rows (lev.n x 3) of a level of a chain built with surf_nullspace = 3."""
+    cnt = vemg_get_size(h, "lev.n", chain, level)
+    out = np.zeros((max(cnt, 1), 3))
+    _check(lib().vemg_get_nullspace(h.h, chain, level, C.c_void_p(out.ctypes.data)), "vemg_get_nullspace")
     return out[:cnt]
 
 
