@@ -140,8 +140,9 @@ def test_fixed_iteration_iterates_match(name):
         err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
         record("fixed_iteration_iterates_match", case=name, k=k, rel_l2=err)
         assert err <= XTOL[name], (k, err)
-        # the recursive residual norms, in units of ||b||
-        assert abs(ig["relres"] - ro["relres"]) <= XTOL[name]
+        # the recursive residual norms, in units of ||b|| (CG's residual may grow above ||b|| on the
+        # way: relative to it then)
+        assert abs(ig["relres"] - ro["relres"]) <= XTOL[name] * max(1.0, ro["relres"])
 
 
 @pytest.mark.parametrize("name", ["box16", "zjit24", "zjit64", "clust32"])
