@@ -58,6 +58,8 @@ def parse():
                     help="additive (the paper's preconditioner), vl_sor or sa (its two comparison forms)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the other configurations (xy-jittered mesh, batched, serving) after the headline")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving workload: this many Poisson-arrival requests (512 for the full stream)")
@@ -359,45 +361,146 @@ def measure(args, h, B, n, ws, rank, local, dist, V, torch, probe, cycle="launch
     return out
 
 
-def run_serve(args):
+def serve_stream(nreq, slots, precision, rate=0.0):
     """Continuous batching over the serving stream: a saturation run (all requests at t = 0) gives
-    the capacity, then the Poisson run at 80% of it (or --rate) gives the latency percentiles."""
+    the capacity, then the Poisson run at 80% of it (or `rate`) gives the latency percentiles.
+    Returns the per-phase summaries, the Poisson rate and the clocks seen during the Poisson run."""
     import torch
     from paper_0912_1976_gb300 import serve as S
-    from paper_0912_1976_gb300 import vemg as V
-    prec = PRECS[args.precision]
-    fac = S.GpuFactory(slots=args.slots, precision=prec)
+    fac = S.GpuFactory(slots=slots, precision=PRECS[precision])
     for i in range(len(S.SIZES)):                  # meshes are inputs: generated before the clock
         fac.mesh(i, 1.0)
     out = {}
-    rate = args.rate
+    clocks = None
     for phase in (["saturation", "poisson"] if not rate else ["poisson"]):
-        reqs = S.make_requests(args.serve, rate=None if phase == "saturation" else rate, seed=5000)
+        reqs = S.make_requests(nreq, rate=None if phase == "saturation" else rate, seed=5000)
         srv = S.Server(fac.build, fac.estimate, fac.free_bytes, fac.rhs, new_x=fac.new_x)
         torch.cuda.synchronize()
+        clk = Clocks(torch.cuda.current_device()) if phase == "poisson" else None
         t0 = time.perf_counter()
         done = srv.run(reqs)
         torch.cuda.synchronize()
         span = time.perf_counter() - t0
+        if clk:
+            clocks = clk.stop()
         out[phase] = dict(S.summarize(done, span), **srv.stats)
         if phase == "saturation":
             rate = 0.8 * out[phase]["requests_per_s"]
         for e in list(srv.cache.values()):
             srv._evict(e)
+    return out, rate, clocks
+
+
+def serve_workload(nreq, rate, slots):
+    return (f"serve{nreq}: Poisson arrivals at {rate:.2f}/s over 8 meshes (44..399 squared x 24 layers, "
+            "z-jitter 0.3), eps in {1e-4,1e-3,1e-2,1e-1}, Neumann/Dirichlet-top 50/50, 1-8 RHS per request, "
+            f"{slots}-slot engines, rtol 1e-8")
+
+
+def run_serve(args):
+    out, rate, clocks = serve_stream(args.serve, args.slots, args.precision, args.rate)
     p = out["poisson"]
     line = {"metric": "serving: solves/s at FP64 rel-res 1e-8, p50/p99 latency", "value": p["solves_per_s"],
             "unit": "solves/s", "n_gpus": 1, "steps": args.serve, "warmup": 0,
             "ms_per_step": 1000.0 * p["makespan_s"] / max(p["requests"], 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision], "data": "synthetic",
-            "config": {"workload": f"serve{args.serve}: Poisson arrivals at {rate:.2f}/s over 8 meshes "
-                                   "(44..399 squared x 24 layers, z-jitter 0.3), eps in {1e-4,1e-3,1e-2,1e-1}, "
-                                   f"Neumann/Dirichlet-top 50/50, 1-8 RHS per request, {args.slots}-slot engines, rtol 1e-8",
-                       "precision": args.precision},
+            "config": {"workload": serve_workload(args.serve, rate, args.slots), "precision": args.precision},
             "p50_latency_ms": p["p50_latency_ms"], "p99_latency_ms": p["p99_latency_ms"],
-            "requests_per_s": p["requests_per_s"], "serving": out}
+            "requests_per_s": p["requests_per_s"], "clocks": clocks, "serving": out}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# --------------------------------------------------------------------------------------------
+# the other configurations, measured in the default run beside the headline
+
+def timed_solves(h, B, steps, warmup, V, torch, batched=False):
+    """Device-timed solves (CUDA events, inputs resident) with the clocks sampled meanwhile."""
+    X = torch.empty_like(B)
+    infos = []
+
+    def one():
+        if batched:
+            _, inf = V.vemg_solve_batch(h, B, X, rtol=RTOL, max_it=2000)
+            return {"iters": max(i["iters"] for i in inf), "true_relres": max(i["true_relres"] for i in inf),
+                    "status": "OK" if all(i["status"] == "OK" for i in inf) else "ENOTCONV"}
+        _, inf = V.vemg_solve(h, B, X, rtol=RTOL, max_it=2000)
+        return inf
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    clk = Clocks(torch.cuda.current_device())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        infos.append(one())
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / steps
+    return {"ms_per_step": ms, "iters": infos[-1]["iters"], "status": infos[-1]["status"],
+            "true_relres_max": max(i["true_relres"] for i in infos), "clocks": clocks}
+
+
+def unstructured_record(V, torch, I):
+    """The 192x192x48 xy-jittered mesh at eps 1e-4: Neumann (surface chain with the near-nullspace
+    {1, x, y}) and Dirichlet top, mixed-precision cycles against plain FP64 PCG on the same GPU."""
+    m = I.make_workload_mesh("xyjit192")
+    vm = V.Mesh.from_inputs(m)
+    A = V.vemg_assemble(vm)
+    b = torch.from_numpy(I.normal_loads(m.n, 2000)).cuda()
+    rec = {"workload": f"xyjit192: 192x192x48 extruded hex->6 tets, {m.n} nodes, H0 1e-4, z-jitter 0.3, "
+                       "xy-jitter 0.2 (redrawn inverted tets), N(0,1) loads, rtol 1e-8",
+           "runs": []}
+    for bc, bcn in ((V.VEMG_NEUMANN, "neumann"), (V.VEMG_DIRICHLET_TOP, "dirichlet_top")):
+        for prec in ("bf16", "fp64"):
+            h = V.vemg_setup(A, vm, V.vemg_default_options(bc=bc, precision=PRECS[prec], surf_nullspace=3))
+            r = timed_solves(h, b, 3, 1, V, torch)
+            r.update(bc=bcn, precision=prec, solves_per_s=1000.0 / r["ms_per_step"],
+                     gdof_iter_per_s=m.n * r["iters"] / (r["ms_per_step"] / 1000.0) / 1e9)
+            rec["runs"].append(r)
+            h.destroy()
+        rb, r64 = rec["runs"][-2], rec["runs"][-1]
+        rb["speedup_over_plain_fp64_pcg"] = r64["ms_per_step"] / rb["ms_per_step"]
+    A.free()
+    rec["note"] = ("at eps 1e-4 the FP64 recursive residual reaches 1e-8 while the true residual stops at the "
+                   "round-off floor (section 6.2: the floor grows as eps decreases); with BF16 precision the "
+                   "{1, x, y} surface chain keeps FP32 values")
+    return rec
+
+
+def batched_record(V, torch, I):
+    """The 384x384x24 mesh with 64 right-hand sides solved together, FP32 V-cycles in FP64 flexible CG
+    against the FP64 batched PCG on the same GPU."""
+    m = I.make_workload_mesh("zjit384x64")
+    vm = V.Mesh.from_inputs(m)
+    A = V.vemg_assemble(vm)
+    k = I.WORKLOADS["zjit384x64"]["nrhs"]
+    B = torch.from_numpy(I.normal_loads(m.n, 4000, k=k)).cuda()
+    rec = {"workload": f"zjit384x64: 384x384x24 extruded hex->6 tets, {m.n} nodes, H0 1e-3, z-jitter 0.3, "
+                       f"{k} N(0,1) right-hand sides mean-zero, rtol 1e-8 per column", "runs": []}
+    for prec in ("fp32", "fp64"):
+        h = V.vemg_setup(A, vm, V.vemg_default_options(precision=PRECS[prec]))
+        r = timed_solves(h, B, 2, 1, V, torch, batched=True)
+        r.update(precision=prec, rhs_per_s=k * 1000.0 / r["ms_per_step"],
+                 gdof_iter_per_s=k * m.n * r["iters"] / (r["ms_per_step"] / 1000.0) / 1e9)
+        rec["runs"].append(r)
+        h.destroy()
+    rec["runs"][0]["speedup_over_fp64_batched"] = rec["runs"][1]["ms_per_step"] / rec["runs"][0]["ms_per_step"]
+    A.free()
+    return rec
+
+
+def serving_record():
+    out, rate, clocks = serve_stream(512, 8, "bf16")
+    p = out["poisson"]
+    return {"workload": serve_workload(512, rate, 8), "precision": "bf16 (FP64 V-cycles at eps <= 1e-4)",
+            "solves_per_s": p["solves_per_s"], "requests_per_s": p["requests_per_s"],
+            "p50_latency_ms": p["p50_latency_ms"], "p99_latency_ms": p["p99_latency_ms"],
+            "columns_converged": p["columns_converged"], "columns_at_floor": p["columns_at_floor"],
+            "columns_failed": p["columns_failed"], "clocks": clocks, "phases": out}
 
 
 def case_phases(args, m, h, V, torch):
@@ -622,6 +725,15 @@ def main():
                "sample": f"one full oracle solve of the {args.workload} workload ({r['iters']} iterations, "
                          f"{r['solve_s']:.1f} s; oracle setup {r['setup_s']:.1f} s not counted)"}
 
+    extra = {}
+    if ws == 1 and not args.headline_only and args.workload == WORKLOAD and not args.rhs:
+        torch.cuda.empty_cache()
+        extra["unstructured"] = unstructured_record(V, torch, I)
+        torch.cuda.empty_cache()
+        extra["batched"] = batched_record(V, torch, I)
+        torch.cuda.empty_cache()
+        extra["serving"] = serving_record()
+
     if rank == 0:
         other = [p for p in res if p != args.precision]
         comparator = None
@@ -647,6 +759,7 @@ def main():
                 "hierarchy_bytes": head["hierarchy_bytes"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": head["clocks"],
                 "plain_fp64_pcg": comparator, "fp32_values": fp32_line}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
