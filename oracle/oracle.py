@@ -15,6 +15,7 @@ import scipy.sparse as sp
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "vemg_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
+LIB_OMP = os.path.join(HERE, "liboracle_omp.so")   # the OpenMP timing build
 
 BC_NEUMANN = 0
 BC_DIRICHLET_TOP = 1
@@ -29,23 +30,25 @@ COARSE_MAX = 512
 MAX_LEVELS = 10
 
 
-def build_oracle(force: bool = False) -> str:
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
-                               "-shared", "-fPIC", "-o", tmp, SRC, "-lm"])
-        os.replace(tmp, LIB)
-    return LIB
+def build_oracle(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle (plain, single-threaded) or its OpenMP timing build (the same source with
+    -fopenmp: row loops on all cores, sums in fixed blocks, the same bits)."""
+    out = LIB_OMP if openmp else LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11"] +
+                              (["-fopenmp"] if openmp else []) + ["-shared", "-fPIC", "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        build_oracle()
-        L = C.CDLL(LIB)
+def lib(openmp: bool = False):
+    if openmp not in _libs:
+        path = build_oracle(openmp=True) if openmp else (build_oracle(), LIB)[1]
+        L = C.CDLL(path)
         dp, ip, u8p = C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_uint8)
         L.or_setup.restype = C.c_void_p
         L.or_setup.argtypes = [C.c_int, dp, C.c_int, ip, u8p, C.c_int, ip, C.c_int, C.c_double,
@@ -77,8 +80,10 @@ def lib():
         L.or_round_bf16.argtypes = [C.c_double]
         L.or_round_bf16.restype = C.c_double
         L.or_round_operators_bf16.argtypes = [C.c_void_p]
-        _lib = L
-    return _lib
+        L.or_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
+        _libs[openmp] = L
+    return _libs[openmp]
 
 
 def _p(a, t):
@@ -101,8 +106,8 @@ class Problem:
     """Oracle setup of one mesh: ordering, A, E~, E~^T A E~, and the two SA chains."""
 
     def __init__(self, mesh, bc: int = BC_NEUMANN, theta=THETA, omega_p=OMEGA_P, coarse_max=COARSE_MAX,
-                 max_levels=MAX_LEVELS, natural_order=False, precond=PC_ADDITIVE, surf_ns=1):
-        L = lib()
+                 max_levels=MAX_LEVELS, natural_order=False, precond=PC_ADDITIVE, surf_ns=1, openmp=False):
+        L = self.L = lib(openmp)
         self._keep = (_f64(mesh.xyz), _i32(mesh.tets), np.ascontiguousarray(mesh.tags, dtype=np.uint8),
                       _i32(mesh.top_tris))
         xyz, tets, tags, tris = self._keep
@@ -118,11 +123,11 @@ class Problem:
 
     def __del__(self):
         if getattr(self, "h", None):
-            lib().or_free(self.h)
+            self.L.or_free(self.h)
             self.h = None
 
     def size(self, key, which=1, level=0) -> int:
-        return int(lib().or_size(self.h, key.encode(), which, level))
+        return int(self.L.or_size(self.h, key.encode(), which, level))
 
     def csr(self, name, which=1, level=0) -> sp.csr_matrix:
         shapes = {"A": (self.n, self.n), "E": (self.n, self.mtop), "ET": (self.mtop, self.n),
@@ -138,7 +143,7 @@ class Problem:
         rp = np.zeros(nrow + 1, np.int32)
         ci = np.zeros(max(nnz, 1), np.int32)
         v = np.zeros(max(nnz, 1), np.float64)
-        rc = lib().or_get_csr(self.h, name.encode(), which, level, _p(rp, C.c_int), _p(ci, C.c_int),
+        rc = self.L.or_get_csr(self.h, name.encode(), which, level, _p(rp, C.c_int), _p(ci, C.c_int),
                               _p(v, C.c_double))
         if rc:
             raise OracleError(f"no matrix {name}")
@@ -147,7 +152,7 @@ class Problem:
     def ints(self, name, which=1, level=0) -> np.ndarray:
         cnt = self.n if name in ("new2old", "tri_of") else self.size("lev.n", which, level)
         out = np.zeros(cnt, np.int32)
-        rc = lib().or_get_int(self.h, name.encode(), which, level, _p(out, C.c_int))
+        rc = self.L.or_get_int(self.h, name.encode(), which, level, _p(out, C.c_int))
         if rc:
             raise OracleError(f"no int array {name}")
         return out
@@ -156,7 +161,7 @@ class Problem:
         """Near-nullspace rows (lev.n x nsd) of a level of a {1, x, y} chain."""
         nsd = self.size("nsd", which)
         out = np.zeros((self.size("lev.n", which, level), nsd))
-        rc = lib().or_get_nullspace(self.h, which, level, _p(out, C.c_double))
+        rc = self.L.or_get_nullspace(self.h, which, level, _p(out, C.c_double))
         if rc:
             raise OracleError("no near-nullspace rows")
         return out
@@ -170,7 +175,7 @@ class Problem:
     def load(self, f):
         f = _f64(f)
         b = np.zeros(self.n)
-        lib().or_load(self.h, _p(f, C.c_double), _p(b, C.c_double))
+        self.L.or_load(self.h, _p(f, C.c_double), _p(b, C.c_double))
         return b
 
     def solve(self, b, tol=1e-8, maxit=1000, flexible=False, hist_len=1000):
@@ -180,7 +185,7 @@ class Problem:
         rr, tr = C.c_double(0), C.c_double(0)
         hist = np.zeros(hist_len)
         coef = np.zeros(2 * maxit + 2)
-        st = lib().or_solve(self.h, _p(b, C.c_double), _p(x, C.c_double), tol, maxit, int(flexible),
+        st = self.L.or_solve(self.h, _p(b, C.c_double), _p(x, C.c_double), tol, maxit, int(flexible),
                             C.byref(it), C.byref(rr), C.byref(tr), _p(hist, C.c_double), hist_len,
                             _p(coef, C.c_double), len(coef))
         k = it.value
@@ -196,25 +201,25 @@ class Problem:
     def precond(self, r):
         r = _f64(r)
         z = np.zeros(self.nunk())
-        lib().or_precond(self.h, _p(r, C.c_double), _p(z, C.c_double))
+        self.L.or_precond(self.h, _p(r, C.c_double), _p(z, C.c_double))
         return z
 
     def spmv(self, x):
         x = _f64(x)
         y = np.zeros(self.nunk())
-        lib().or_spmv(self.h, _p(x, C.c_double), _p(y, C.c_double))
+        self.L.or_spmv(self.h, _p(x, C.c_double), _p(y, C.c_double))
         return y
 
     def vcycle(self, which, b):
         b = _f64(b)
         x = np.zeros_like(b)
-        lib().or_vcycle(self.h, which, _p(b, C.c_double), _p(x, C.c_double))
+        self.L.or_vcycle(self.h, which, _p(b, C.c_double), _p(x, C.c_double))
         return x
 
     def round_operators_bf16(self):
         """Round the stored cycle operators to BF16 (off-diagonals of every level matrix, P and
         P^T), in place: the operator the BF16 variant of the cycle applies."""
-        lib().or_round_operators_bf16(self.h)
+        self.L.or_round_operators_bf16(self.h)
 
 
 def round_bf16(a: float) -> float:

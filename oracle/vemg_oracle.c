@@ -7,7 +7,10 @@
  * leg may load this library. The product path (libvemg) shares no code with it.
  *
  * Build: gcc -O2 -ffp-contract=off -shared -fPIC (no fused multiply-add, so that every
- * floating-point decision in the setup is reproducible bit for bit).
+ * floating-point decision in the setup is reproducible bit for bit). A timing build adds -fopenmp:
+ * the solve's row loops (SpMV, the rows of one SOR colour, residuals, transfers, vector updates)
+ * then run on all host cores, and every sum over a vector is taken in fixed blocks of OR_BLOCK
+ * entries added in block order, so that both builds give the same bits whatever the thread count.
  *
  * What it computes, in the paper's order and notation:
  *   - P1 stiffness matrix A of -Laplace(phi) with all-Neumann boundaries (section 3, Eq. Ax=b)
@@ -37,6 +40,12 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#define OR_PARALLEL_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define OR_PARALLEL_FOR
+#endif
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -210,6 +219,7 @@ static csr galerkin(const csr *A, const csr *P, const csr *PT) {
 }
 
 static void csr_spmv(const csr *a, const double *x, double *y) {
+    OR_PARALLEL_FOR
     for (int i = 0; i < a->n; ++i) {
         double s = 0.0;
         for (int k = a->rp[i]; k < a->rp[i + 1]; ++k) s += a->v[k] * x[a->ci[k]];
@@ -217,16 +227,57 @@ static void csr_spmv(const csr *a, const double *x, double *y) {
     }
 }
 
+/* Sums over vectors: the partial sums of fixed blocks of OR_BLOCK entries (each in index order),
+   added in block order. The blocks do not depend on the number of threads. */
+#define OR_BLOCK 4096
+
 static double dot(int n, const double *a, const double *b) {
+    int nb = (n + OR_BLOCK - 1) / OR_BLOCK;
+    double *part = (double *)xcalloc((size_t)(nb > 0 ? nb : 1), sizeof(double));
+    OR_PARALLEL_FOR
+    for (int k = 0; k < nb; ++k) {
+        double s = 0.0;
+        int hi = (k + 1) * OR_BLOCK < n ? (k + 1) * OR_BLOCK : n;
+        for (int i = k * OR_BLOCK; i < hi; ++i) s += a[i] * b[i];
+        part[k] = s;
+    }
     double s = 0.0;
-    for (int i = 0; i < n; ++i) s += a[i] * b[i];
+    for (int k = 0; k < nb; ++k) s += part[k];
+    free(part);
     return s;
 }
 
 static double vsum(int n, const double *a) {
+    int nb = (n + OR_BLOCK - 1) / OR_BLOCK;
+    double *part = (double *)xcalloc((size_t)(nb > 0 ? nb : 1), sizeof(double));
+    OR_PARALLEL_FOR
+    for (int k = 0; k < nb; ++k) {
+        double s = 0.0;
+        int hi = (k + 1) * OR_BLOCK < n ? (k + 1) * OR_BLOCK : n;
+        for (int i = k * OR_BLOCK; i < hi; ++i) s += a[i];
+        part[k] = s;
+    }
     double s = 0.0;
-    for (int i = 0; i < n; ++i) s += a[i];
+    for (int k = 0; k < nb; ++k) s += part[k];
+    free(part);
     return s;
+}
+
+/* the number of threads the solve's loops use (1 without OpenMP) */
+int or_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -963,6 +1014,8 @@ static void sor_sweep(const chain *C, const level *L, const double *b, double *x
     }
     for (int cc = 0; cc < L->ncolours; ++cc) {
         int c = forward ? cc : L->ncolours - 1 - cc;
+        /* the rows of one colour are not coupled: any order gives the same values */
+        OR_PARALLEL_FOR
         for (int k = L->cptr[c]; k < L->cptr[c + 1]; ++k) sor_row(&L->A, b, x, L->crow[k]);
     }
 }
@@ -1017,10 +1070,12 @@ static void vcycle(const chain *C, int l, const double *b, double *x) {
     memset(x, 0, sizeof(double) * (size_t)n);
     sor_sweep(C, L, b, x, 1);
     csr_spmv(&L->A, x, L->r);
+    OR_PARALLEL_FOR
     for (int i = 0; i < n; ++i) L->r[i] = b[i] - L->r[i];
     const level *Nx = &C->lv[l + 1];
     csr_spmv(&L->PT, L->r, Nx->b);
     vcycle(C, l + 1, Nx->b, Nx->x);
+    OR_PARALLEL_FOR
     for (int i = 0; i < n; ++i) {
         double s = 0.0;
         for (int k = L->P.rp[i]; k < L->P.rp[i + 1]; ++k) s += L->P.v[k] * Nx->x[L->P.ci[k]];
@@ -1426,6 +1481,7 @@ void or_precond(void *hp, const double *r, double *z) {
     csr_spmv(&h->E, s0->x, z);
     level *b0 = &h->bar.lv[0];
     vcycle(&h->bar, 0, r + mt, b0->x);
+    OR_PARALLEL_FOR
     for (int i = 0; i < n - mt; ++i) z[mt + i] += b0->x[i];
 }
 
@@ -1463,7 +1519,11 @@ int or_solve(void *hp, const double *b_orig, double *x_orig, double tol, int max
     if (bn == 0.0) goto out;
     memcpy(r, b, sizeof(double) * (size_t)m);
     or_precond(h, r, z);
-    if (neu) { double mu = vsum(m, z) / (double)m; for (int i = 0; i < m; ++i) z[i] -= mu; }
+    if (neu) {
+        double mu = vsum(m, z) / (double)m;
+        OR_PARALLEL_FOR
+        for (int i = 0; i < m; ++i) z[i] -= mu;
+    }
     memcpy(p, z, sizeof(double) * (size_t)m);
     double rz = dot(m, r, z);
     status = OR_ENOTCONV;
@@ -1473,6 +1533,7 @@ int or_solve(void *hp, const double *b_orig, double *x_orig, double tol, int max
         if (!(pq > 0.0)) { status = OR_EBREAKDOWN; break; }
         double alpha = rz / pq;
         if (coef && 2 * k < coef_len) coef[2 * k] = alpha;
+        OR_PARALLEL_FOR
         for (int i = 0; i < m; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
         double rn = sqrt(dot(m, r, r));
         *iters = k + 1;
@@ -1481,7 +1542,11 @@ int or_solve(void *hp, const double *b_orig, double *x_orig, double tol, int max
         if (!(rn == rn)) { status = OR_EBREAKDOWN; break; }
         if (rn <= tol * bn) { status = OR_OK; break; }
         or_precond(h, r, z);
-        if (neu) { double mu = vsum(m, z) / (double)m; for (int i = 0; i < m; ++i) z[i] -= mu; }
+        if (neu) {
+            double mu = vsum(m, z) / (double)m;
+            OR_PARALLEL_FOR
+            for (int i = 0; i < m; ++i) z[i] -= mu;
+        }
         double beta;
         if (flexible) {
             beta = -dot(m, z, q) / pq;
@@ -1491,16 +1556,14 @@ int or_solve(void *hp, const double *b_orig, double *x_orig, double tol, int max
             rz = rzn;
         }
         if (coef && 2 * k + 1 < coef_len) coef[2 * k + 1] = beta;
+        OR_PARALLEL_FOR
         for (int i = 0; i < m; ++i) p[i] = z[i] + beta * p[i];
         if (flexible) rz = dot(m, r, z);
     }
     if (neu) { double mu = vsum(m, x) / (double)m; for (int i = 0; i < m; ++i) x[i] -= mu; }
     or_spmv(h, x, q);
-    {
-        double s = 0.0;
-        for (int i = 0; i < m; ++i) { double d = b[i] - q[i]; s += d * d; }
-        *true_relres = sqrt(s) / bn;
-    }
+    for (int i = 0; i < m; ++i) q[i] = b[i] - q[i];
+    *true_relres = sqrt(dot(m, q, q)) / bn;
 out:
     for (int i = 0; i < h->n; ++i) x_orig[i] = 0.0;
     for (int i = 0; i < m; ++i) x_orig[h->new2old[off + i]] = x[i];

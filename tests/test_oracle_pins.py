@@ -1080,3 +1080,19 @@ def test_section62_linear_nullspace_gives_eps_independent_rate_on_unstructured_m
     assert max(it[3]) <= 1.1 * min(it[3]), it
     assert it[1][-1] >= 1.8 * it[1][0], it
     assert it[3][-1] * 3 <= it[1][-1], it
+
+
+def test_openmp_timing_build_gives_the_same_bits():
+    """The OpenMP build of the oracle (its timing build on all host cores) runs the solve's row loops
+    in parallel and sums vectors in fixed blocks, so x, the iteration count and every residual are
+    the same bits as the single-threaded build's, whatever the number of threads."""
+    m = _mesh(20, 8, h0=1e-3, zj=0.3)
+    b = I.normal_loads(m.n, 31)
+    r1 = O.Problem(m).solve(b, tol=1e-9)
+    Lo = O.lib(openmp=True)
+    for t in (1, 3, 4):
+        Lo.or_set_threads(t)
+        assert Lo.or_threads() == t
+        r = O.Problem(m, openmp=True).solve(b, tol=1e-9)
+        assert r["iters"] == r1["iters"] and r["relres"] == r1["relres"]
+        assert np.array_equal(r["x"].view(np.uint64), r1["x"].view(np.uint64))
