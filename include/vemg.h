@@ -211,7 +211,10 @@ int vemg_engine_create(vemg_hierarchy *h, int slots, void *stream, vemg_engine *
 void vemg_engine_destroy(vemg_engine *e);
 
 /* Copy b (device, caller order) into a free slot, project it (Neumann) and start its iteration at
-   the next step. *slot receives the slot; VEMG_ENOMEM if no slot is free. Asynchronous. */
+   the next step. *slot receives the slot; VEMG_ENOMEM if no slot is free. Asynchronous: b_dev is
+   read by kernels on the engine's stream, so it must hold its values when that stream reaches
+   them (order its producer before, e.g. an event the engine's stream waits on) and must stay
+   allocated until they have run (the engine's stream has passed this call). */
 int vemg_engine_admit(vemg_engine *e, const double *b_dev, double rtol, int max_it, int *slot);
 
 /* Enqueue `iters` iterations of every occupied slot and a copy of the slot states (asynchronous;

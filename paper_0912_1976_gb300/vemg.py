@@ -503,6 +503,13 @@ class Engine:
             self.e = C.c_void_p(None)
 
     def admit(self, b_dev: torch.Tensor, rtol=1e-8, max_it=1000) -> int:
+        """The engine's stream reads b_dev: it first waits for the caller's current stream (where b
+        was produced), and the caching allocator keeps b's memory until the engine's stream has
+        passed the copy."""
+        cur = torch.cuda.current_stream(b_dev.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+            b_dev.record_stream(self.stream)
         slot = C.c_int()
         _check(lib().vemg_engine_admit(self.e, _dev(b_dev), rtol, max_it, C.byref(slot)), "vemg_engine_admit")
         return slot.value
@@ -519,6 +526,11 @@ class Engine:
         return st.value, info.as_dict()
 
     def retire(self, slot, x_dev: torch.Tensor):
+        """x_dev is written on the engine's stream, which the call synchronises; it first waits for
+        the caller's stream, where x_dev was allocated."""
+        cur = torch.cuda.current_stream(x_dev.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
         _check(lib().vemg_engine_retire(self.e, slot, _dev(x_dev)), "vemg_engine_retire")
 
     def free_slots(self) -> int:
