@@ -501,7 +501,8 @@ def batched_record(V, torch, I):
         h = V.vemg_setup(A, vm, V.vemg_default_options(precision=PRECS[prec]))
         r = timed_solves(h, B, 2, 1, V, torch, batched=True)
         r.update(precision=prec, rhs_per_s=k * 1000.0 / r["ms_per_step"],
-                 gdof_iter_per_s=k * m.n * r["iters"] / (r["ms_per_step"] / 1000.0) / 1e9)
+                 gdof_iter_per_s=k * m.n * r["iters"] / (r["ms_per_step"] / 1000.0) / 1e9,
+                 launch_shapes=V.vemg_batch_tuning(h))
         rec["runs"].append(r)
         h.destroy()
     rec["runs"][0]["speedup_over_fp64_batched"] = rec["runs"][1]["ms_per_step"] / rec["runs"][0]["ms_per_step"]

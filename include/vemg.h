@@ -203,6 +203,18 @@ int vemg_solve_batch(vemg_hierarchy *h, int k, const double *B_dev, int64_t ldb,
    engine owns its work memory (vemg_engine_bytes); one engine per hierarchy at a time. */
 typedef struct vemg_engine vemg_engine;
 
+/* Launch shapes of the batched solve's row kernels (the paper has no counterpart: an autotuner of
+   this implementation). Three classes: 0 = colour sweeps, 1 = the other V-cycle operations,
+   2 = the outer FP64 operations (A p, the true residual, E~ and E~^T). Each has kw lanes per row
+   (4, 8, 16 or 32; each lane takes the columns lane, lane + kw, ...) and warps per block (2, 4, 8).
+   The first batched solve (or engine) of a width K times every candidate shape on this
+   hierarchy's finest level and outer operator and keeps the fastest of each class; the results do
+   not depend on the shapes. vemg_batch_tuning reports the batch width and the shapes in use with
+   their measured launch times in microseconds (VEMG_EINVAL before any batched solve);
+   vemg_batch_set_tuning imposes shapes for width K (allocating its work if needed). */
+int vemg_batch_tuning(const vemg_hierarchy *h, int *K, int *kw3, int *warps3, float *us3);
+int vemg_batch_set_tuning(vemg_hierarchy *h, int K, const int *kw3, const int *warps3, void *stream);
+
 #define VEMG_SLOT_FREE 0
 #define VEMG_SLOT_RUNNING 1
 #define VEMG_SLOT_DONE 2    /* converged, broken down or out of iterations: retire it */

@@ -25,9 +25,18 @@ namespace vemg {
 static constexpr int kBT = 512;        // their threads
 static constexpr int kBU = 8;          // entries loaded per round trip in a batched row
 static constexpr int kMaxK = 128;      // widest batch
-static constexpr int kSellWarps = 4;   // warps per block in the batched sliced-ELL kernels
+static constexpr int kSellWarps = 4;   // warps per block of the batched row kernels (untuned default)
+static constexpr int kMaxWarps = 8;    // most warps per block the autotuner tries
 
 static thread_local int64_t *b_count = nullptr;
+struct BTune;
+static thread_local const BTune *b_tune = nullptr;   // launch shapes of the batch being recorded
+
+struct TuneScope {
+    const BTune *saved;
+    explicit TuneScope(const BTune *t) : saved(b_tune) { b_tune = t; }
+    ~TuneScope() { b_tune = saved; }
+};
 #define BATCH_LAUNCHED()         \
     do {                         \
         VEMG_CHECK_LAUNCH();     \
@@ -77,7 +86,19 @@ struct BatchGraphs {
     int64_t k_pre = 0, k_body = 0, k_post = 0;
 };
 
+// Launch shapes of the batched row kernels, by class: 0 = colour sweeps, 1 = the other V-cycle
+// operations (residuals, restrictions, prolongations), 2 = the outer FP64 operations (A p, the
+// true residual, E~ and E~^T). kw: lanes per row (each lane takes columns lane, lane + kw, ...),
+// warps: warps per block. Chosen per batch width by timing the candidates (autotune below); the
+// per-column arithmetic is the same for every shape.
+struct BTune {
+    int kw[3] = {0, 0, 0}, warps[3] = {0, 0, 0};   // 0: the untuned default
+    float us[3] = {0.f, 0.f, 0.f};                  // the chosen shapes' measured launch times
+    int tried = 0;                                   // candidate launches timed
+};
+
 struct BatchWork {
+    BTune tune;
     int K = 0;
     double *X = nullptr, *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr, *B = nullptr;
     void *lx[2][kMaxLevels] = {}, *lb[2][kMaxLevels] = {}, *lr[2][kMaxLevels] = {};
@@ -116,7 +137,7 @@ __global__ void k_bto_float(int64_t n, const double *__restrict__ a, float *__re
 // c = lane % KW + j KW. SOR skips the diagonal entry and, when sweeping from x = 0 (cur >= 0), every
 // entry whose column has colour >= cur (not yet visited: zero). RES keeps the diagonal: y = b - A x.
 template <int OP, class VT, class XT, class BT, class YT, class AT, int KW>
-__global__ void __launch_bounds__(32 * kSellWarps) k_bcsr(int nrows, const int *__restrict__ rows, int r0, CsrP A,
+__global__ void __launch_bounds__(32 * kMaxWarps) k_bcsr(int nrows, const int *__restrict__ rows, int r0, CsrP A,
                                                          const VT *__restrict__ dg, const BT *__restrict__ b,
                                                          const XT *x, YT *y, int K, const int *__restrict__ colour,
                                                          int cur) {
@@ -177,7 +198,7 @@ __global__ void __launch_bounds__(32 * kSellWarps) k_bcsr(int nrows, const int *
 
 // one lane per row and column group (K = 1, 2): entries loaded kBU at a time
 template <int OP, class VT, class XT, class BT, class YT, class AT, int KW>
-__global__ void __launch_bounds__(32 * kSellWarps) k_bcsr_narrow(int nrows, const int *__restrict__ rows, int r0,
+__global__ void __launch_bounds__(32 * kMaxWarps) k_bcsr_narrow(int nrows, const int *__restrict__ rows, int r0,
                                                                 CsrP A, const VT *__restrict__ dg,
                                                                 const BT *__restrict__ b, const XT *x, YT *y, int K,
                                                                 const int *__restrict__ colour, int cur) {
@@ -215,24 +236,30 @@ __global__ void __launch_bounds__(32 * kSellWarps) k_bcsr_narrow(int nrows, cons
     else y[e] = (YT)((AT)b[e] - acc);
 }
 
+// cls: the launch-shape class of the call (BTune); kw, nw > 0 force a shape (autotuning)
 template <int OP, class VT, class XT, class BT, class YT, class AT>
 static void bcsr(CsrP A, int nrows, const int *rows, int r0, const VT *dg, const BT *b, const XT *x, YT *y, int K,
-                 const int *colour, int cur, cudaStream_t s) {
+                 const int *colour, int cur, cudaStream_t s, int cls = 1, int kw = 0, int nw = 0) {
     if (nrows <= 0) return;
-    int KW = std::min(K, 32);
-    dim3 blk(32 * kSellWarps);
+    if (kw <= 0 && b_tune && b_tune->kw[cls] > 0) {
+        kw = b_tune->kw[cls];
+        nw = b_tune->warps[cls];
+    }
+    int KW = std::min(K, kw > 0 ? kw : 32);
+    const int wpb = nw > 0 ? nw : kSellWarps;
+    dim3 blk(32 * wpb);
     if (KW < 4) {
         int64_t t = (int64_t)nrows * KW;
         if (KW == 1)
-            pdl_launch(k_bcsr_narrow<OP, VT, XT, BT, YT, AT, 1>, grid_for(t, 32 * kSellWarps), blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+            pdl_launch(k_bcsr_narrow<OP, VT, XT, BT, YT, AT, 1>, grid_for(t, 32 * wpb), blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
         else
-            pdl_launch(k_bcsr_narrow<OP, VT, XT, BT, YT, AT, 2>, grid_for(t, 32 * kSellWarps), blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+            pdl_launch(k_bcsr_narrow<OP, VT, XT, BT, YT, AT, 2>, grid_for(t, 32 * wpb), blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
         BATCH_LAUNCHED();
         return;
     }
     int RW = 32 / KW;
     int64_t warps = (nrows + RW - 1) / RW;
-    int grid = (int)((warps + kSellWarps - 1) / kSellWarps);
+    int grid = (int)((warps + wpb - 1) / wpb);
     switch (KW) {
         case 4: pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 4>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
         case 8: pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 8>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
@@ -261,7 +288,7 @@ static void bsweep(const BLevel &L, const BT *b, XT *x, bool forward, bool from_
         int c = forward ? cc : L.ncolours - 1 - cc;
         int nrows = L.cptr[c + 1] - L.cptr[c];
         bcsr<BOP_SOR, XT, XT, BT, XT, XT>(A, nrows, L.crow + L.cptr[c], 0, (const XT *)L.dinv, b, x, x, K, L.colour,
-                                         from_zero ? c : -1, s);
+                                         from_zero ? c : -1, s, 0);
     }
 }
 
@@ -597,7 +624,7 @@ static void bprecond(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
         // surface branch: r_c = E~^T r in FP64, one V-cycle on E~^T A E~
         bcsr<BOP_SPMV, double, double, double, XT, double>(CsrP{h->ET.rp, h->ET.ci, h->ET.v}, h->mtop, nullptr, 0,
                                                            (const double *)nullptr, (const double *)nullptr, W->R,
-                                                           b0, K, nullptr, -1, h->side);
+                                                           b0, K, nullptr, -1, h->side, 2);
         bvcycle<XT, XT>(*W->bsurf, W, 0, 0, (const XT *)b0, x0, h->side);
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_join, h->side));
         const int64_t nbk = (int64_t)(h->n - mt) * K;
@@ -613,11 +640,11 @@ static void bprecond(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
         if (std::is_same<XT, float>::value && W->Ev32)
             bcsr<BOP_SPMV, float, XT, double, double, float>(CsrP{h->E.rp, h->E.ci, W->Ev32}, h->n, nullptr, 0,
                                                             (const float *)nullptr, (const double *)nullptr, x0,
-                                                            W->Z, K, nullptr, -1, s);
+                                                            W->Z, K, nullptr, -1, s, 2);
         else
             bcsr<BOP_SPMV, double, XT, double, double, double>(CsrP{h->E.rp, h->E.ci, h->E.v}, h->n, nullptr, 0,
                                                                (const double *)nullptr, (const double *)nullptr, x0,
-                                                               W->Z, K, nullptr, -1, s);
+                                                               W->Z, K, nullptr, -1, s, 2);
         pdl_launch(k_badd<XT>, grid_for(nbk, 256), 256, s, nbk, (const XT *)xb, W->Z + (int64_t)mt * K, 0);
         BATCH_LAUNCHED();
     } else {
@@ -686,7 +713,7 @@ static void bphase_step(vemg_hierarchy *h, BatchWork *W, cudaStream_t s, cudaGra
     const int K = W->K;
     const int64_t N = (int64_t)h->nu * K;
     bcsr<BOP_SPMV, double, double, double, double, double>(W->Aout, h->nu, nullptr, 0, (const double *)nullptr,
-                                                           (const double *)nullptr, W->P, W->Q, K, nullptr, -1, s);
+                                                           (const double *)nullptr, W->P, W->Q, K, nullptr, -1, s, 2);
     {
         BSums d{{W->P}, {W->Q}, 1};
         bsums(W, N, d, s);
@@ -721,7 +748,7 @@ static void bphase_post(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
     }
     // true residual into Q
     bcsr<BOP_RES, double, double, double, double, double>(W->Aout, h->nu, nullptr, 0, (const double *)nullptr, W->B,
-                                                          W->X, W->Q, K, nullptr, -1, s);
+                                                          W->X, W->Q, K, nullptr, -1, s, 2);
     BSums d{{W->Q}, {W->Q}, 1};
     bsums(W, N, d, s);
     bstage2(h, W, ST_TRUE, 1, N, 0, s);
@@ -872,6 +899,85 @@ static BatchWork *batch_work(vemg_hierarchy *h, int K, cudaStream_t s) {
     return h->batch;
 }
 
+// The autotuner: for each class of row kernel, every candidate shape (lanes per row 4, 8, 16, 32
+// up to K; 2, 4 or 8 warps per block) is launched on a representative operation of this
+// hierarchy at this batch width (class 0: the largest colour of the finest A_bar level swept
+// over all its entries; class 1: the residual of that level; class 2: the outer q = A p), one
+// warm-up and two timed launches each (CUDA events), and the fastest shape is kept. The vectors
+// are the batch's own work buffers (zeroed); the per-column arithmetic does not depend on the shape.
+template <class XT>
+static void autotune_t(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
+    const int K = W->K;
+    const BLevel &L = W->bbar->lv[0];
+    XT *lx = (XT *)W->lx[1][0], *lb = (XT *)W->lb[1][0], *lr = (XT *)W->lr[1][0];
+    const size_t vb = sizeof(XT) * (size_t)L.n * K;
+    VEMG_CHECK_CUDA(cudaMemsetAsync(lx, 0, vb, s));
+    VEMG_CHECK_CUDA(cudaMemsetAsync(lb, 0, vb, s));
+    VEMG_CHECK_CUDA(cudaMemsetAsync(W->P, 0, sizeof(double) * (size_t)h->nu * K, s));
+    int cbig = 0;
+    for (int c = 1; c < L.ncolours; ++c)
+        if (L.cptr[c + 1] - L.cptr[c] > L.cptr[cbig + 1] - L.cptr[cbig]) cbig = c;
+    const CsrP A{L.rp, L.ci, L.v};
+    cudaEvent_t e0, e1;
+    VEMG_CHECK_CUDA(cudaEventCreate(&e0));
+    VEMG_CHECK_CUDA(cudaEventCreate(&e1));
+    int64_t *saved = b_count;
+    b_count = nullptr;
+    try {
+        for (int cls = 0; cls < 3; ++cls) {
+            float best = 0.f;
+            for (int kw : {4, 8, 16, 32}) {
+                if (kw > K) continue;
+                for (int wp : {2, 4, 8}) {
+                    auto run = [&]() {
+                        if (cls == 0)
+                            bcsr<BOP_SOR, XT, XT, XT, XT, XT>(A, L.cptr[cbig + 1] - L.cptr[cbig], L.crow + L.cptr[cbig], 0,
+                                                               (const XT *)L.dinv, lb, lx, lx, K, L.colour, -1, s, 0,
+                                                               kw, wp);
+                        else if (cls == 1)
+                            bcsr<BOP_RES, XT, XT, XT, XT, XT>(A, L.n, nullptr, 0, (const XT *)nullptr, lb, lx, lr, K,
+                                                               nullptr, -1, s, 1, kw, wp);
+                        else
+                            bcsr<BOP_SPMV, double, double, double, double, double>(
+                                W->Aout, h->nu, nullptr, 0, (const double *)nullptr, (const double *)nullptr, W->P,
+                                W->Q, K, nullptr, -1, s, 2, kw, wp);
+                    };
+                    run();
+                    VEMG_CHECK_CUDA(cudaEventRecord(e0, s));
+                    run();
+                    run();
+                    VEMG_CHECK_CUDA(cudaEventRecord(e1, s));
+                    VEMG_CHECK_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    VEMG_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    const float us = 500.f * ms;   // per launch
+                    W->tune.tried++;
+                    if (W->tune.kw[cls] == 0 || us < best) {
+                        best = us;
+                        W->tune.kw[cls] = kw;
+                        W->tune.warps[cls] = wp;
+                        W->tune.us[cls] = us;
+                    }
+                }
+            }
+        }
+    } catch (...) {
+        b_count = saved;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    b_count = saved;
+    VEMG_CHECK_CUDA(cudaEventDestroy(e0));
+    VEMG_CHECK_CUDA(cudaEventDestroy(e1));
+}
+
+static void autotune(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
+    if (W->K < 4) return;   // one lane per row and column: no shape to choose
+    if (h->precision != VEMG_PREC_FP64) autotune_t<float>(h, W, s);
+    else autotune_t<double>(h, W, s);
+}
+
 BatchWork *new_batch_work(vemg_hierarchy *h, int K, cudaStream_t s) {
     BatchWork *W = new BatchWork();
     W->K = K;
@@ -916,6 +1022,14 @@ BatchWork *new_batch_work(vemg_hierarchy *h, int K, cudaStream_t s) {
     W->ctr = ar.alloc<unsigned>(2);
     VEMG_CHECK_CUDA(cudaMemsetAsync(W->ctr, 0, sizeof(unsigned) * 2, s));
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
+    try {
+        autotune(h, W, s);
+    } catch (...) {
+        W->arena.release();
+        delete W;
+        throw;
+    }
+    VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
     return W;
 }
 
@@ -927,6 +1041,7 @@ int solve_batch(vemg_hierarchy *h, int k, const double *Bin, int64_t ldb, double
     int K = 1;
     while (K < k) K *= 2;
     BatchWork *W = batch_work(h, K, s);
+    TuneScope tune(&W->tune);
     b_count = &h->launches;
     const int nu = h->nu;
     k_binit<<<1, 1, 0, s>>>(W->sc, K, rtol, max_it);
@@ -1132,6 +1247,7 @@ int vemg_engine_create(vemg_hierarchy *h, int slots, void *stream, vemg_engine *
         k_engine_init<<<1, 1, 0, s>>>(e->W->sc, K);
         VEMG_CHECK_LAUNCH();
         // one iteration of every occupied column, as a graph
+        TuneScope tune(&e->W->tune);
         cudaStream_t cs;
         VEMG_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         int64_t count = 0;
@@ -1288,6 +1404,44 @@ int vemg_engine_retire(vemg_engine *e, int slot, double *x_dev) {
         return err.code;
     }
     e->used[slot] = 0;
+    return VEMG_OK;
+}
+
+int vemg_batch_tuning(const vemg_hierarchy *h, int *K, int *kw, int *warps, float *us) {
+    if (!h || !K || !kw || !warps || !us) return VEMG_EINVAL;
+    if (!h->batch) return VEMG_EINVAL;
+    const BTune &t = h->batch->tune;
+    *K = h->batch->K;
+    for (int c = 0; c < 3; ++c) {
+        kw[c] = t.kw[c];
+        warps[c] = t.warps[c];
+        us[c] = t.us[c];
+    }
+    return VEMG_OK;
+}
+
+int vemg_batch_set_tuning(vemg_hierarchy *h, int K, const int *kw, const int *warps, void *stream) {
+    if (!h || !kw || !warps || K < 1 || K > kMaxK || (K & (K - 1)) || h->precond == VEMG_PRECOND_NONE)
+        return VEMG_EINVAL;
+    for (int c = 0; c < 3; ++c)
+        if (!(kw[c] == 4 || kw[c] == 8 || kw[c] == 16 || kw[c] == 32) || !(warps[c] == 2 || warps[c] == 4 ||
+                                                                          warps[c] == 8))
+            return VEMG_EINVAL;
+    try {
+        cudaStream_t s = (cudaStream_t)stream;
+        prepare_solve(h, s);
+        BatchWork *W = batch_work(h, K, s);
+        for (int c = 0; c < 3; ++c) {
+            W->tune.kw[c] = kw[c];
+            W->tune.warps[c] = warps[c];
+            W->tune.us[c] = 0.f;
+        }
+        release_batch_graphs(W);   // recaptured with the new shapes at the next solve
+    } catch (const Error &err) {
+        return err.code;
+    } catch (...) {
+        return VEMG_EINTERNAL;
+    }
     return VEMG_OK;
 }
 

@@ -109,63 +109,70 @@ static double sell_bytes(int64_t nnz, double vb, int64_t rows, double per_row) {
 // entries of a sliced-ELL row loaded per chunk (before their gathers)
 static constexpr int kU = 16;
 
+// the V-cycle kernels' chunk: 8 entries with FP64 values (16 FP64 values and their columns held
+// 80 registers and measured 11% slower per FP64-cycle solve), 16 with FP32 or BF16 values
+template <class VT>
+__host__ __device__ constexpr int cycle_chunk() {
+    return sizeof(VT) == sizeof(double) ? 8 : kU;
+}
+
 // BF16 values widen to FP32 before they meet the vector; FP32 and FP64 values pass through
 __device__ __forceinline__ float float_or_self(__nv_bfloat16 a) { return __bfloat162float(a); }
 __device__ __forceinline__ float float_or_self(float a) { return a; }
 __device__ __forceinline__ double float_or_self(double a) { return a; }
 
-// The first kU entries of a sliced-ELL row (column indices and values), loaded before the
+// The first U entries of a sliced-ELL row (column indices and values), loaded before the
 // kernel waits for its predecessor: the operators are setup data that no solve kernel writes,
 // so these loads overlap the previous kernel and only the gathers of x remain after the wait.
-template <class VT>
+template <class VT, int U = kU>
 struct RowHead {
-    int c[kU];
-    VT a[kU];
+    int c[U];
+    VT a[U];
 };
 
-template <class VT>
-__device__ __forceinline__ void load_head(RowHead<VT> &h, const int *__restrict__ col, const VT *__restrict__ v, int o,
-                                          int w) {
+template <class VT, int U>
+__device__ __forceinline__ void load_head(RowHead<VT, U> &h, const int *__restrict__ col, const VT *__restrict__ v,
+                                          int o, int w) {
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
+    for (int u = 0; u < U; ++u) {
         h.c[u] = u < w ? __ldg(col + o + 32 * u) : 0;
         h.a[u] = u < w ? __ldg(v + o + 32 * u) : VT{};
     }
 }
 
-// Dot product of one sliced-ELL row with x: the head's entries, then the rest of the row kU
+// Dot product of one sliced-ELL row with x: the head's entries, then the rest of the row U
 // entries at a time (column indices and values first, then the gathers), so that a row costs
-// two dependent memory round trips per kU entries instead of two per entry. lim >= 0 skips
-// columns >= lim.
-template <class VT, class XT, class AT>
-__device__ __forceinline__ AT sell_row(const RowHead<VT> &h, const int *__restrict__ col, const VT *__restrict__ v,
+// two dependent memory round trips per U entries instead of two per entry. lim >= 0 skips
+// columns >= lim. The products are added in the row's stored order whatever U is.
+template <class VT, class XT, class AT, int U>
+__device__ __forceinline__ AT sell_row(const RowHead<VT, U> &h, const int *__restrict__ col, const VT *__restrict__ v,
                                        int o, int w, const XT *x, int lim) {
     AT acc = 0;
 #pragma unroll
-    for (int u = 0; u < kU; ++u)
+    for (int u = 0; u < U; ++u)
         if (u < w && (lim < 0 || h.c[u] < lim)) acc = fmadd((AT)(float_or_self(h.a[u])), (AT)x[h.c[u]], acc);
-    for (int k0 = kU; k0 < w; k0 += kU) {
-        int c[kU];
-        VT a[kU];
+    for (int k0 = U; k0 < w; k0 += U) {
+        int c[U];
+        VT a[U];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
+        for (int u = 0; u < U; ++u) {
             int k = k0 + u;
             c[u] = k < w ? __ldg(col + o + 32 * k) : 0;
             a[u] = k < w ? __ldg(v + o + 32 * k) : VT{};
         }
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
+        for (int u = 0; u < U; ++u)
             if (k0 + u < w && (lim < 0 || c[u] < lim)) acc = fmadd((AT)(float_or_self(a[u])), (AT)x[c[u]], acc);
     }
     return acc;
 }
 
-template <class VT, class XT, class AT>
+template <class VT, class XT, class AT, int U = kU>
 __device__ __forceinline__ AT sell_row(const int *__restrict__ col, const VT *__restrict__ v, int o, int w,
                                        const XT *x, int lim) {
-    RowHead<VT> h;
+    RowHead<VT, U> h;
     load_head(h, col, v, o, w);
-    return sell_row<VT, XT, AT>(h, col, v, o, w, x, lim);
+    return sell_row<VT, XT, AT, U>(h, col, v, o, w, x, lim);
 }
 
 // y = A x (add: y += A x) over the slices [s0, s1); accumulation in AT. With x0: the restriction
@@ -181,7 +188,8 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_spmv(int s0, int s1, const 
     int s = s0 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     const bool active = s < s1 && lane < nrow[s];
-    RowHead<VT> h;
+    constexpr int U = cycle_chunk<VT>();
+    RowHead<VT, U> h;
     int o = 0, w = 0, r = 0;
     YT d0 = 0;
     if (active) {
@@ -193,7 +201,7 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_spmv(int s0, int s1, const 
     }
     pdl_begin();
     if (!active) return;
-    AT acc = sell_row<VT, XT, AT>(h, col, v, o, w, x, -1);
+    AT acc = sell_row<VT, XT, AT, U>(h, col, v, o, w, x, -1);
     YT yr = add ? (YT)((AT)y[r] + acc) : (YT)acc;
     y[r] = yr;
     if (x0 && r < lim0) x0[r] = yr * d0;
@@ -211,7 +219,8 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_sor(int s0, int s1, const i
     int s = s0 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     const bool active = s < s1 && lane < nrow[s];
-    RowHead<VT> h;
+    constexpr int U = cycle_chunk<VT>();
+    RowHead<VT, U> h;
     int o = 0, w = 0, r = 0;
     XT di = 0;
     if (active) {
@@ -223,7 +232,7 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_sor(int s0, int s1, const i
     }
     pdl_begin();
     if (!active) return;
-    XT acc = sell_row<VT, XT, XT>(h, col, v, o, w, x, lim);
+    XT acc = sell_row<VT, XT, XT, U>(h, col, v, o, w, x, lim);
     x[r] = ((XT)b[r] - acc) * di;
 }
 
@@ -238,7 +247,8 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_residual(int nsl, const int
     int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     const bool active = s < nsl && lane < nrow[s];
-    RowHead<VT> h;
+    constexpr int U = cycle_chunk<VT>();
+    RowHead<VT, U> h;
     int o = 0, w = 0, i = 0;
     XT dg = 0;
     if (active) {
@@ -250,7 +260,7 @@ __global__ void __launch_bounds__(kSellBlock) k_sell_residual(int nsl, const int
     }
     pdl_begin();
     if (!active) return;
-    XT acc = fmadd(dg, x[i], sell_row<VT, XT, XT>(h, col, v, o, w, x, -1));
+    XT acc = fmadd(dg, x[i], sell_row<VT, XT, XT, U>(h, col, v, o, w, x, -1));
     r[i] = (XT)b[i] - acc;
 }
 

@@ -86,6 +86,9 @@ PROTOTYPES = {
     "vemg_get_csr": (C.c_int, [_VP, C.c_char_p, C.c_int, C.c_int, _VP, _VP, _VP]),
     "vemg_get_int": (C.c_int, [_VP, C.c_char_p, C.c_int, C.c_int, _VP]),
     "vemg_get_nullspace": (C.c_int, [_VP, C.c_int, C.c_int, _VP]),
+    "vemg_batch_tuning": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                    C.POINTER(C.c_float)]),
+    "vemg_batch_set_tuning": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _VP]),
     "vemg_spmv": (C.c_int, [_VP, _DP, _DP, _VP]),
     "vemg_precond": (C.c_int, [_VP, _DP, _DP, _VP]),
     "vemg_vcycle": (C.c_int, [_VP, C.c_int, _DP, _DP, _VP]),
@@ -376,6 +379,23 @@ def vemg_get_nullspace(h: Hierarchy, chain=0, level=0) -> np.ndarray:
     out = np.zeros((max(cnt, 1), 3))
     _check(lib().vemg_get_nullspace(h.h, chain, level, C.c_void_p(out.ctypes.data)), "vemg_get_nullspace")
     return out[:cnt]
+
+
+BATCH_CLASSES = ("sweep", "cycle", "outer")
+
+
+def vemg_batch_tuning(h: Hierarchy) -> dict:
+    """Launch shapes the batched solves of this hierarchy use (after its first batched solve)."""
+    K = C.c_int()
+    kw, wp, us = (C.c_int * 3)(), (C.c_int * 3)(), (C.c_float * 3)()
+    _check(lib().vemg_batch_tuning(h.h, C.byref(K), kw, wp, us), "vemg_batch_tuning")
+    return {"K": K.value, **{c: {"lanes_per_row": kw[i], "warps_per_block": wp[i], "us_per_launch": us[i]}
+                             for i, c in enumerate(BATCH_CLASSES)}}
+
+
+def vemg_batch_set_tuning(h: Hierarchy, K: int, kw, warps, stream=None):
+    a, b = (C.c_int * 3)(*kw), (C.c_int * 3)(*warps)
+    _check(lib().vemg_batch_set_tuning(h.h, K, a, b, _stream(stream)), "vemg_batch_set_tuning")
 
 
 def vemg_spmv(h: Hierarchy, x_dev, y_dev=None, stream=None):

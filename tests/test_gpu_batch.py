@@ -79,3 +79,30 @@ def test_batch_dirichlet_top():
         assert infos[c]["status"] == "OK" and abs(infos[c]["iters"] - i1["iters"]) <= 1
         assert torch.all(X[c][tops] == 0)
         assert (X[c] - x1).norm().item() <= 1e-8 * x1.norm().item()
+
+
+def test_autotuner_picks_a_launch_shape_per_kernel_class():
+    m, vm, A, h = _setup()
+    B = _rhs(m.n, 5, 400)                     # batch width 8
+    V.vemg_solve_batch(h, B, rtol=1e-8, max_it=300)
+    t = V.vemg_batch_tuning(h)
+    assert t["K"] == 8
+    for cls in V.BATCH_CLASSES:
+        assert t[cls]["lanes_per_row"] in (4, 8) and t[cls]["warps_per_block"] in (2, 4, 8)
+        assert t[cls]["us_per_launch"] > 0.0
+
+
+def test_batched_results_do_not_depend_on_launch_shapes():
+    """The shapes change which lanes and blocks do the work, not the arithmetic of a column: the
+    same iterations and the same bits for every imposed shape."""
+    m, vm, A, h = _setup(precision=V.VEMG_PREC_FP32)
+    B = _rhs(m.n, 6, 500)
+    out = []
+    for kw, wp in ((4, 2), (8, 8), (4, 4)):
+        V.vemg_batch_set_tuning(h, 8, [kw] * 3, [wp] * 3)
+        X, infos = V.vemg_solve_batch(h, B, rtol=1e-9, max_it=300)
+        assert V.vemg_batch_tuning(h)["sweep"]["lanes_per_row"] == kw
+        out.append((X.clone(), [i["iters"] for i in infos]))
+    for X, it in out[1:]:
+        assert it == out[0][1]
+        assert torch.equal(X, out[0][0])
