@@ -720,6 +720,13 @@ def main():
         # 192x192x32 mesh (colour 2, 261,577 rows): 1.07 (FP32 values) / 1.09 (BF16 values) x its
         # algorithmic bytes, scaled here by this workload's bytes per launch
         traffic = None
+        if dom == "sor_coarse" and args.precision == "bf16":
+            # three captured coarse launches on a 192x192x32 mesh moved 0.606-0.623 MB from DRAM each
+            # (L2 hit rate 33-36%); the class mixes launches of every coarse level, so the figure is
+            # the captured launches' own, not scaled to this workload's average launch
+            traffic = {"bytes_per_launch": 0.6167e6,
+                       "source": "ncu dram__bytes (read + write), mean of 3 k_sell_sor<__nv_bfloat16, float, float> "
+                                 "launches on a 192x192x32 mesh (profiles/sor_coarse_bf16_zjit192.md); not scaled"}
         if dom == "sor_fine" and args.precision in SOR_FINE_DRAM_RATIO:
             traffic = {"bytes_per_launch": SOR_FINE_DRAM_RATIO[args.precision] * c["bytes_per_launch"],
                        "source": f"ncu dram__bytes (read + write) of one {SOR_FINE_KERNEL[args.precision]} launch "
