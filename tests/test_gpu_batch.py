@@ -106,3 +106,28 @@ def test_batched_results_do_not_depend_on_launch_shapes():
     for X, it in out[1:]:
         assert it == out[0][1]
         assert torch.equal(X, out[0][0])
+
+
+def test_batched_columns_match_the_oracle_above_a_million_nodes():
+    """The batched solve at scale (160x160x40, 1,082,841 nodes, four right-hand sides, FP32 cycles
+    in FP64 flexible CG as in the 64-right-hand-side configuration) against the oracle's FP64 PCG
+    of each column (its OpenMP build: the same bits as the plain one)."""
+    from conftest import record
+    m = I.make_mesh(160, 160, 40, I.depth_sines(1e-3), z_jitter=0.3, seed=43)
+    vm = V.Mesh.from_inputs(m)
+    A = V.vemg_assemble(vm)
+    h = V.vemg_setup(A, vm, V.vemg_default_options(precision=V.VEMG_PREC_FP32))
+    B = _rhs(m.n, 4, 600)
+    X, infos = V.vemg_solve_batch(h, B, rtol=1e-8, max_it=300)
+    om = O.Problem(m, openmp=True)
+    worst = 0.0
+    for c in range(4):
+        ro = om.solve(B[c].cpu().numpy(), tol=1e-8)
+        assert infos[c]["status"] == "OK" and ro["status"] == "OK"
+        assert abs(infos[c]["iters"] - ro["iters"]) <= 2
+        err = np.linalg.norm(X[c].cpu().numpy() - ro["x"]) / np.linalg.norm(ro["x"])
+        worst = max(worst, err)
+        assert err <= 1e-8, (c, err)
+        assert infos[c]["true_relres"] <= 2e-8
+    record("batched_vs_oracle_1M", n=m.n, worst_rel_l2=worst, iters=[i["iters"] for i in infos])
+    h.destroy()
