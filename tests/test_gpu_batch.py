@@ -109,7 +109,7 @@ def test_batched_results_do_not_depend_on_launch_shapes():
 
 
 def test_batched_columns_match_the_oracle_above_a_million_nodes():
-    """The batched solve at scale (160x160x40, 1,082,841 nodes, four right-hand sides, FP32 cycles
+    """The batched solve at scale (160x160x40, 1,062,761 nodes, four right-hand sides, FP32 cycles
     in FP64 flexible CG as in the 64-right-hand-side configuration) against the oracle's FP64 PCG
     of each column (its OpenMP build: the same bits as the plain one)."""
     from conftest import record
