@@ -10,6 +10,8 @@ from oracle import oracle as O
 from paper_0912_1976_gb300 import inputs as I
 from paper_0912_1976_gb300 import vemg as V
 
+from conftest import record
+
 pytestmark = pytest.mark.gpu
 
 
@@ -34,8 +36,16 @@ def test_pcg_coefficients_match_oracle(bc):
     k = 6
     assert np.allclose(a[:k], ro["alpha"][:k], rtol=1e-9, atol=0)
     assert bt[0] == 0.0 and np.allclose(bt[1:k], ro["beta"][1:k], rtol=1e-9, atol=0)
+    # the k-step tridiagonals differ by the coefficients' rounding, and a symmetric eigenvalue
+    # moves by at most the perturbation's norm: their extremes agree closely
+    lo_k, hi_k = V.vemg_lanczos_extremes(a[:k], bt[:k])
+    lo_ko, hi_ko = V.vemg_lanczos_extremes(ro["alpha"][:k], ro["beta"][:k])
+    assert abs(lo_k - lo_ko) <= 1e-7 * lo_ko and abs(hi_k - hi_ko) <= 1e-7 * hi_ko
+    # the full history's extremes move with the drifted late coefficients
     lo, hi = V.vemg_lanczos_extremes(a, bt)
     lo_o, hi_o = V.vemg_lanczos_extremes(ro["alpha"], ro["beta"])
+    record("spectrum_ritz", bc=bc, k_step_lo=abs(lo_k - lo_ko) / lo_ko, k_step_hi=abs(hi_k - hi_ko) / hi_ko,
+           full_lo=abs(lo - lo_o) / lo_o, full_hi=abs(hi - hi_o) / hi_o)
     assert abs(lo - lo_o) <= 1e-3 * lo_o and abs(hi - hi_o) <= 1e-3 * hi_o
 
 
