@@ -234,8 +234,14 @@ int vemg_engine_admit(vemg_engine *e, const double *b_dev, double rtol, int max_
 int vemg_engine_launch(vemg_engine *e, int iters);
 int vemg_engine_wait(vemg_engine *e);
 
-/* State of a slot after the last wait: VEMG_SLOT_FREE / RUNNING / DONE, and its info (iters,
-   status, recursive relres; true_relres = -1: not computed). */
+/* Whether the engine's stream still has work (*busy = 1) or has completed everything enqueued on
+   it (*busy = 0), without waiting. After *busy = 0 the slot states are those of the last launch,
+   as after vemg_engine_wait; a server can thus step every engine at its own pace. */
+int vemg_engine_query(const vemg_engine *e, int *busy);
+
+/* State of a slot after the last wait (or a query that found the engine idle): VEMG_SLOT_FREE /
+   RUNNING / DONE, and its info (iters, status, recursive relres; true_relres = -1: not
+   computed). */
 int vemg_engine_poll(const vemg_engine *e, int slot, vemg_info *info, int *state);
 
 /* Copy the slot's x (device, caller order, zero mean for Neumann, 0 on top nodes for Dirichlet-top)

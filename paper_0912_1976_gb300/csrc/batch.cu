@@ -1353,6 +1353,21 @@ int vemg_engine_wait(vemg_engine *e) {
     return VEMG_OK;
 }
 
+int vemg_engine_query(const vemg_engine *e, int *busy) {
+    if (!e || !busy) return VEMG_EINVAL;
+    cudaError_t err = cudaStreamQuery(e->s);
+    if (err == cudaErrorNotReady) {
+        *busy = 1;
+        return VEMG_OK;
+    }
+    if (err != cudaSuccess) {
+        set_last_cuda_error(err, "cudaStreamQuery", __FILE__, __LINE__);
+        return VEMG_ECUDA;
+    }
+    *busy = 0;
+    return VEMG_OK;
+}
+
 int vemg_engine_poll(const vemg_engine *e, int slot, vemg_info *info, int *state) {
     if (!e || !state || slot < 0 || slot >= (int)e->used.size()) return VEMG_EINVAL;
     if (!e->used[slot]) {

@@ -82,6 +82,48 @@ void dev_free_raw(void *p) {
     }
 }
 
+static thread_local bool t_scratch_on = false;
+static thread_local cudaStream_t t_scratch_s = nullptr;
+
+ScratchStream::ScratchStream(cudaStream_t s) : prev_on(t_scratch_on), prev_s(t_scratch_s) {
+    t_scratch_on = true;
+    t_scratch_s = s;
+}
+
+ScratchStream::~ScratchStream() {
+    t_scratch_on = prev_on;
+    t_scratch_s = prev_s;
+}
+
+void *scratch_alloc(size_t bytes, bool *ordered, cudaStream_t *s) {
+    bool custom;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        custom = g_alloc.alloc != nullptr;
+    }
+    *ordered = false;
+    if (!t_scratch_on || custom) return dev_alloc_raw(bytes);
+    void *p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes > 0 ? bytes : 1, t_scratch_s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        throw Error{VEMG_ENOMEM};
+    }
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
+        throw Error{VEMG_ECUDA};
+    }
+    *ordered = true;
+    *s = t_scratch_s;
+    return p;
+}
+
+void scratch_free(void *p, bool ordered, cudaStream_t s) {
+    if (!p) return;
+    if (ordered) cudaFreeAsync(p, s);
+    else dev_free_raw(p);
+}
+
 template <class F>
 static int guarded(F &&f) {
     try {
@@ -223,6 +265,7 @@ int vemg_set_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(void *, v
 int vemg_assemble(const vemg_mesh *mesh, vemg_csr *A_out, void *stream) {
     return guarded([&] {
         if (!mesh || !A_out) return VEMG_EINVAL;
+        ScratchStream scratch((cudaStream_t)stream);
         assemble(mesh, A_out, (cudaStream_t)stream);
         return VEMG_OK;
     });
@@ -282,6 +325,7 @@ int vemg_setup(const vemg_csr *A, const vemg_mesh *mesh, const vemg_options *opt
         h->precision = o.precision;
         h->precond = (o.bc == VEMG_DIRICHLET_TOP && o.precond != VEMG_PRECOND_NONE) ? VEMG_PRECOND_ADDITIVE
                                                                                    : o.precond;
+        ScratchStream scratch((cudaStream_t)stream);
         setup(h, A, mesh, (cudaStream_t)stream);
         prepare_solve(h, (cudaStream_t)stream);
         return VEMG_OK;

@@ -96,15 +96,32 @@ struct Arena {
     }
 };
 
+// While one of these lives on a thread (and no caller allocator is installed), that thread's
+// Scratch buffers come from the device's memory pool in the order of stream s: releasing one does
+// not wait for the whole device, so a setup does not stall behind other streams' work.
+struct ScratchStream {
+    bool prev_on;
+    cudaStream_t prev_s;
+    explicit ScratchStream(cudaStream_t s);
+    ~ScratchStream();
+    ScratchStream(const ScratchStream &) = delete;
+    ScratchStream &operator=(const ScratchStream &) = delete;
+};
+// *ordered: whether the block is stream-ordered (then released on *s)
+void *scratch_alloc(size_t bytes, bool *ordered, cudaStream_t *s);
+void scratch_free(void *p, bool ordered, cudaStream_t s);
+
 // Temporary device buffer freed at scope exit.
 template <class T>
 struct Scratch {
     T *p = nullptr;
+    bool ordered = false;
+    cudaStream_t s = nullptr;
     explicit Scratch(int64_t count) {
         size_t b = (size_t)(count > 0 ? count : 1) * sizeof(T);
-        p = (T *)dev_alloc_raw(b);
+        p = (T *)scratch_alloc(b, &ordered, &s);
     }
-    ~Scratch() { dev_free_raw(p); }
+    ~Scratch() { scratch_free(p, ordered, s); }
     Scratch(const Scratch &) = delete;
     Scratch &operator=(const Scratch &) = delete;
     operator T *() const { return p; }

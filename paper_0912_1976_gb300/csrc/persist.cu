@@ -630,18 +630,19 @@ void build_persist(vemg_hierarchy *h, cudaStream_t s) {
         P->bar = ar.alloc<unsigned long long>(kBarStride * (int)groups.size());
         P->err = ar.alloc<int>(1);
         P->cycles = ar.alloc<unsigned long long>(std::max(P->nphases, 1));
-        VEMG_CHECK_CUDA(cudaMemset(P->cycles, 0, sizeof(unsigned long long) * std::max(P->nphases, 1)));
+        // every copy on the caller's stream (which may not order itself after the legacy stream)
+        VEMG_CHECK_CUDA(cudaMemsetAsync(P->cycles, 0, sizeof(unsigned long long) * std::max(P->nphases, 1), s));
         for (size_t g = 0; g < groups.size(); ++g)
             for (int k = groups[g].z; k < groups[g].w; ++k) {
                 P->op.push_back(B.ph[k].op);
                 P->level.push_back(B.ph[k].level);
                 P->group.push_back((int)g);
             }
-        VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
-        VEMG_CHECK_CUDA(cudaMemcpy(P->phases, B.ph.data(), sizeof(PPhase) * B.ph.size(), cudaMemcpyHostToDevice));
-        VEMG_CHECK_CUDA(cudaMemcpy(P->groups, groups.data(), sizeof(int4) * groups.size(), cudaMemcpyHostToDevice));
-        VEMG_CHECK_CUDA(cudaMemset(P->bar, 0, sizeof(unsigned long long) * kBarStride * groups.size()));
-        VEMG_CHECK_CUDA(cudaMemset(P->err, 0, sizeof(int)));
+        VEMG_CHECK_CUDA(cudaMemcpyAsync(P->phases, B.ph.data(), sizeof(PPhase) * B.ph.size(), cudaMemcpyHostToDevice, s));
+        VEMG_CHECK_CUDA(cudaMemcpyAsync(P->groups, groups.data(), sizeof(int4) * groups.size(), cudaMemcpyHostToDevice, s));
+        VEMG_CHECK_CUDA(cudaMemsetAsync(P->bar, 0, sizeof(unsigned long long) * kBarStride * groups.size(), s));
+        VEMG_CHECK_CUDA(cudaMemsetAsync(P->err, 0, sizeof(int), s));
+        VEMG_CHECK_CUDA(cudaStreamSynchronize(s));   // the host vectors are read before they go
         P->ngroups = (int)groups.size();
         P->grid = grid;
         P->bytes = B.bytes;
@@ -705,8 +706,8 @@ static void build_tail(Arena &ar, SChain &C, bool fp32, int tail_rows, int ncta,
         if (++l0 >= C.nlev) return;
     }
     PPhase *d = ar.alloc<PPhase>((int)B.ph.size());
+    VEMG_CHECK_CUDA(cudaMemcpyAsync(d, B.ph.data(), sizeof(PPhase) * B.ph.size(), cudaMemcpyHostToDevice, s));
     VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
-    VEMG_CHECK_CUDA(cudaMemcpy(d, B.ph.data(), sizeof(PPhase) * B.ph.size(), cudaMemcpyHostToDevice));
     C.tail = d;
     C.tail_n = (int)B.ph.size();
     C.tail_bytes = B.bytes;
@@ -716,7 +717,8 @@ static void build_tail(Arena &ar, SChain &C, bool fp32, int tail_rows, int ncta,
         T->ncta = ncta;
         try {
             T->cycles = ar.alloc<unsigned long long>(C.tail_n);
-            VEMG_CHECK_CUDA(cudaMemset(T->cycles, 0, sizeof(unsigned long long) * C.tail_n));
+            VEMG_CHECK_CUDA(cudaMemsetAsync(T->cycles, 0, sizeof(unsigned long long) * C.tail_n, s));
+            VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
         } catch (...) {
             delete T;
             throw;
@@ -736,7 +738,10 @@ void release_ctail(SChain &C) {
 
 void ctail_profile_reset(SChain &C) {
     auto T = (ClusterTail *)C.ctail;
-    if (T) VEMG_CHECK_CUDA(cudaMemset(T->cycles, 0, sizeof(unsigned long long) * C.tail_n));
+    if (!T) return;
+    // ordered before any later launch on any stream
+    VEMG_CHECK_CUDA(cudaMemset(T->cycles, 0, sizeof(unsigned long long) * C.tail_n));
+    VEMG_CHECK_CUDA(cudaDeviceSynchronize());
 }
 
 // the cluster tail's steps with the persistent program's op codes
@@ -816,7 +821,9 @@ void persist_reset(vemg_hierarchy *h, cudaStream_t s) {
 void persist_profile_reset(vemg_hierarchy *h) {
     Persist *P = h->persist;
     if (!P) return;
+    // ordered before any later launch on any stream
     VEMG_CHECK_CUDA(cudaMemset(P->cycles, 0, sizeof(unsigned long long) * std::max(P->nphases, 1)));
+    VEMG_CHECK_CUDA(cudaDeviceSynchronize());
 }
 
 int persist_profile(vemg_hierarchy *h, int cap, int *count, int *op, int *level, int *group, double *cycles) {

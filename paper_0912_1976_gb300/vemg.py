@@ -98,6 +98,7 @@ PROTOTYPES = {
     "vemg_engine_admit": (C.c_int, [_VP, _DP, C.c_double, C.c_int, C.POINTER(C.c_int)]),
     "vemg_engine_launch": (C.c_int, [_VP, C.c_int]),
     "vemg_engine_wait": (C.c_int, [_VP]),
+    "vemg_engine_query": (C.c_int, [_VP, C.POINTER(C.c_int)]),
     "vemg_engine_poll": (C.c_int, [_VP, C.c_int, C.POINTER(vemg_info), C.POINTER(C.c_int)]),
     "vemg_engine_retire": (C.c_int, [_VP, C.c_int, _DP]),
     "vemg_engine_slots": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -539,6 +540,12 @@ class Engine:
 
     def wait(self):
         _check(lib().vemg_engine_wait(self.e), "vemg_engine_wait")
+
+    def query(self) -> bool:
+        """True when the engine's stream has completed its enqueued work (no waiting)."""
+        busy = C.c_int()
+        _check(lib().vemg_engine_query(self.e, C.byref(busy)), "vemg_engine_query")
+        return busy.value == 0
 
     def poll(self, slot):
         info, st = vemg_info(), C.c_int()
