@@ -27,6 +27,7 @@ static constexpr int kBU = 8;          // entries loaded per round trip in a bat
 static constexpr int kMaxK = 128;      // widest batch
 static constexpr int kSellWarps = 4;   // warps per block of the batched row kernels (untuned default)
 static constexpr int kMaxWarps = 8;    // most warps per block the autotuner tries
+static constexpr int kCpl = 4;        // columns a lane of a batched row kernel takes per pass
 
 static thread_local int64_t *b_count = nullptr;
 struct BTune;
@@ -164,8 +165,13 @@ __global__ void __launch_bounds__(32 * kMaxWarps) k_bcsr(int nrows, const int *_
         if (OP == BOP_SOR && cc0 >= 0 && (cc0 == r || (cur > 0 && __ldg(colour + cc0) >= cur))) cc0 = -1;
     }
     pdl_begin();
-    for (int c = gl; c < K; c += KW) {
-        AT acc = 0;
+    // a lane takes the columns c0, c0 + KW, ..., kCpl of them per pass, so that each entry of the
+    // row issues kCpl independent loads of its neighbour's x row. K and KW are powers of two, so
+    // every lane of the warp makes the same number of passes (the shuffles need all 32).
+    for (int c0 = gl; c0 < K; c0 += kCpl * KW) {
+        AT acc[kCpl];
+#pragma unroll
+        for (int u = 0; u < kCpl; ++u) acc[u] = 0;
         if (!skip_all) {
             for (int k0 = 0; k0 < wmax; k0 += KW) {
                 int k = k0 + gl;
@@ -182,17 +188,27 @@ __global__ void __launch_bounds__(32 * kMaxWarps) k_bcsr(int nrows, const int *_
                     if (jj < nj) {
                         int cj = __shfl_sync(0xffffffffu, cc, gb + jj);
                         VT vj = __shfl_sync(0xffffffffu, vv, gb + jj);
-                        if (cj >= 0) acc += (AT)vj * (AT)x[(int64_t)cj * K + c];
+                        if (cj >= 0) {
+                            const XT *xr = x + (int64_t)cj * K;
+#pragma unroll
+                            for (int u = 0; u < kCpl; ++u)
+                                if (c0 + u * KW < K) acc[u] += (AT)vj * (AT)xr[c0 + u * KW];
+                        }
                     }
                 }
             }
         }
         if (!valid) continue;
-        int64_t e = (int64_t)r * K + c;
-        if (OP == BOP_SPMV) y[e] = (YT)acc;
-        else if (OP == BOP_SPMV_ADD) y[e] = (YT)((AT)y[e] + acc);
-        else if (OP == BOP_SOR) y[e] = (YT)(((AT)b[e] - acc) * (AT)dg[r]);
-        else y[e] = (YT)((AT)b[e] - acc);
+#pragma unroll
+        for (int u = 0; u < kCpl; ++u) {
+            const int c = c0 + u * KW;
+            if (c >= K) continue;
+            int64_t e = (int64_t)r * K + c;
+            if (OP == BOP_SPMV) y[e] = (YT)acc[u];
+            else if (OP == BOP_SPMV_ADD) y[e] = (YT)((AT)y[e] + acc[u]);
+            else if (OP == BOP_SOR) y[e] = (YT)(((AT)b[e] - acc[u]) * (AT)dg[r]);
+            else y[e] = (YT)((AT)b[e] - acc[u]);
+        }
     }
 }
 
