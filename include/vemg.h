@@ -340,8 +340,7 @@ int vemg_vcycle(vemg_hierarchy *h, int chain, const double *b_dev, double *x_dev
    hierarchies of at most 1,048,576 unknowns; a larger hierarchy is rejected with VEMG_EINVAL
    (vemg_last_error gives the count). Every device that loads libvemg holds that array until the
    process exits. The first call on a device looks up the array's device address
-   (cudaGetSymbolAddress) with that device current; make that first call before any stream
-   capture. All calls share the one array: calls whose GPU work overlaps (several streams or host
+   (cudaGetSymbolAddress) with that device current. All calls share the one array: calls whose GPU work overlaps (several streams or host
    threads at once) race and give wrong results. The array needs no clearing: each call writes
    every entry it later reads. x_dev and y_dev are device arrays in the internal order, as for
    vemg_spmv. Each call synchronises the stream (cudaStreamSynchronize) before it returns. */

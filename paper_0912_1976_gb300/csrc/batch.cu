@@ -27,7 +27,10 @@ static constexpr int kBU = 8;          // entries loaded per round trip in a bat
 static constexpr int kMaxK = 128;      // widest batch
 static constexpr int kSellWarps = 4;   // warps per block of the batched row kernels (untuned default)
 static constexpr int kMaxWarps = 8;    // most warps per block the autotuner tries
-static constexpr int kCpl = 4;        // columns a lane of a batched row kernel takes per pass
+// columns a lane of a batched row kernel takes per pass: 8 with FP32 accumulators, 4 with FP64
+// ones (8 FP64 accumulators spill)
+template <class AT>
+__host__ __device__ constexpr int cols_per_lane() { return sizeof(AT) == 4 ? 8 : 4; }
 
 static thread_local int64_t *b_count = nullptr;
 struct BTune;
@@ -168,6 +171,7 @@ __global__ void __launch_bounds__(32 * kMaxWarps) k_bcsr(int nrows, const int *_
     // a lane takes the columns c0, c0 + KW, ..., kCpl of them per pass, so that each entry of the
     // row issues kCpl independent loads of its neighbour's x row. K and KW are powers of two, so
     // every lane of the warp makes the same number of passes (the shuffles need all 32).
+    constexpr int kCpl = cols_per_lane<AT>();
     for (int c0 = gl; c0 < K; c0 += kCpl * KW) {
         AT acc[kCpl];
 #pragma unroll
