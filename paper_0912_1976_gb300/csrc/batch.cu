@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kBT) k_bsums(int64_t N, int K, BSums d, double
 #pragma unroll
     for (int j = 0; j < kBE; ++j)
 #pragma unroll
-        for (int s = 0; s < NS; ++s) acc[s] += va[s][j] * vb[s][j];
+        for (int s = 0; s < NS; ++s) acc[s] = fma(va[s][j], vb[s][j], acc[s]);
     bblock_partials<NS>(acc, K, part);
 }
 
@@ -545,26 +545,45 @@ __global__ void __launch_bounds__(256) k_bstage2(int op, int nblk, int ns, int K
 }
 
 // b -= mean (Neumann), r = b, x = p = 0 (streaming, no reduction)
+// rb32 (FP32 V-cycles on two chains): the FP32 copy of r's A_bar part (elements from off32 on),
+// the finest A_bar level's right-hand side; every kernel that writes r writes it too
 __global__ void k_bprepare(int64_t N, int K, int neumann, double *__restrict__ b, double *__restrict__ r,
-                           double *__restrict__ x, double *__restrict__ p, const double *__restrict__ sc) {
+                           double *__restrict__ x, double *__restrict__ p, const double *__restrict__ sc,
+                           float *__restrict__ rb32, int64_t off32) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= N) return;
     double bi = b[e] - (neumann ? sc[B_BMEAN * K + (int)(e & (K - 1))] : 0.0);
     b[e] = bi;
     r[e] = bi;
+    if (rb32 && e >= off32) rb32[e - off32] = (float)bi;
     x[e] = 0.0;
     p[e] = 0.0;
 }
 
-// X += alpha P, R -= alpha Q per column
-__global__ void k_bupdate_xr(int64_t N, int K, const double *__restrict__ p, const double *__restrict__ q,
-                             double *__restrict__ x, double *__restrict__ r, const double *__restrict__ sc) {
+// X += alpha P, R -= alpha Q per column, the FP32 copy of R's A_bar part, and the stage-1 sums
+// of R * R: the elements of a thread and the order of its sum are those of k_bsums, so the
+// partials are the same bits as a separate pass would give
+__global__ void __launch_bounds__(kBT) k_bupdate_xr(int64_t N, int K, const double *__restrict__ p,
+                                                    const double *__restrict__ q, double *__restrict__ x,
+                                                    double *__restrict__ r, const double *__restrict__ sc,
+                                                    float *__restrict__ rb32, int64_t off32, double *part) {
     pdl_begin();
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= N) return;
-    double a = sc[B_ALPHA * K + (int)(e & (K - 1))];
-    x[e] += a * p[e];
-    r[e] -= a * q[e];
+    double acc[1] = {0.0};
+    const int64_t base = (int64_t)blockIdx.x * kBT * kBE + threadIdx.x;
+    const double a = sc[B_ALPHA * K + (int)(base & (K - 1))];   // kBT is a multiple of K: one column
+#pragma unroll
+    for (int j = 0; j < kBE; ++j) {
+        const int64_t e = base + (int64_t)j * kBT;
+        double rn = 0.0;
+        if (e < N) {
+            x[e] = fma(a, p[e], x[e]);
+            rn = fma(-a, q[e], r[e]);
+            r[e] = rn;
+            if (rb32 && e >= off32) rb32[e - off32] = (float)rn;
+        }
+        acc[0] = fma(rn, rn, acc[0]);
+    }
+    bblock_partials<1>(acc, K, part);
 }
 
 // z += x (assign: z = x)
@@ -648,9 +667,7 @@ static void bprecond(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
         bvcycle<XT, XT>(*W->bsurf, W, 0, 0, (const XT *)b0, x0, h->side);
         VEMG_CHECK_CUDA(cudaEventRecord(h->ev_join, h->side));
         const int64_t nbk = (int64_t)(h->n - mt) * K;
-        if (std::is_same<XT, float>::value && W->Rb32) {
-            pdl_launch(k_bto_float, grid_for(nbk, 256), 256, s, nbk, (const double *)(W->R + (int64_t)mt * K), W->Rb32);
-            BATCH_LAUNCHED();
+        if (std::is_same<XT, float>::value && W->Rb32) {   // kept current by every writer of r
             bvcycle<XT, XT>(*W->bbar, W, 1, 0, (const XT *)W->Rb32, xb, s);
         } else {
             bvcycle<XT, double>(*W->bbar, W, 1, 0, W->R + (int64_t)mt * K, xb, s);
@@ -673,6 +690,11 @@ static void bprecond(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
         pdl_launch(k_badd<XT>, grid_for(N, 256), 256, s, N, (const XT *)xb, W->Z, 1);
         BATCH_LAUNCHED();
     }
+}
+
+// the first element of r's A_bar part (the FP32 copy covers it)
+static int64_t rb32_offset(const vemg_hierarchy *h, const BatchWork *W) {
+    return single_chain(h) ? 0 : (int64_t)h->mtop * W->K;
 }
 
 static void bsums(BatchWork *W, int64_t N, const BSums &d, cudaStream_t s) {
@@ -722,7 +744,7 @@ static void bphase_pre(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
         bsums(W, N, d, s);
         bstage2(h, W, ST_MEAN_B, 1, N, 0, s);
     }
-    k_bprepare<<<grid_for(N, 256), 256, 0, s>>>(N, K, neu, W->B, W->R, W->X, W->P, W->sc);
+    k_bprepare<<<grid_for(N, 256), 256, 0, s>>>(N, K, neu, W->B, W->R, W->X, W->P, W->sc, W->Rb32, rb32_offset(h, W));
     BATCH_LAUNCHED();
     BSums d{{W->B}, {W->B}, 1};
     bsums(W, N, d, s);
@@ -739,14 +761,10 @@ static void bphase_step(vemg_hierarchy *h, BatchWork *W, cudaStream_t s, cudaGra
         bsums(W, N, d, s);
         bstage2(h, W, ST_ALPHA, 1, N, 0, s);
     }
-    pdl_launch(k_bupdate_xr, grid_for(N, 256), 256, s, N, K, (const double *)W->P, (const double *)W->Q, W->X, W->R,
-               (const double *)W->sc);
+    pdl_launch(k_bupdate_xr, stage1_blocks(N), kBT, s, N, K, (const double *)W->P, (const double *)W->Q, W->X, W->R,
+               (const double *)W->sc, W->Rb32, rb32_offset(h, W), W->part);
     BATCH_LAUNCHED();
-    {
-        BSums d{{W->R}, {W->R}, 1};
-        bsums(W, N, d, s);
-        bstage2(h, W, ST_RN, 1, N, 0, s, hd, use_cond);
-    }
+    bstage2(h, W, ST_RN, 1, N, 0, s, hd, use_cond);
 }
 
 static void bphase_direction(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
@@ -1186,13 +1204,14 @@ __global__ void k_col_gather(int nu, int K, int c, const int *__restrict__ calle
 
 // b -= mean, r = b, x = p = z = q = 0 in column c
 __global__ void k_col_prepare(int nu, int K, int c, const double *__restrict__ sc, double *B, double *R, double *X,
-                              double *P, double *Z, double *Q) {
+                              double *P, double *Z, double *Q, float *rb32, int64_t off32) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nu) return;
     int64_t e = (int64_t)i * K + c;
     double bi = B[e] - sc[B_BMEAN * K + c];
     B[e] = bi;
     R[e] = bi;
+    if (rb32 && e >= off32) rb32[e - off32] = (float)bi;
     X[e] = 0.0;
     P[e] = 0.0;
     Z[e] = 0.0;
@@ -1215,12 +1234,14 @@ __global__ void k_col_scatter(int nu, int K, int c, int neumann, const int *__re
 }
 
 // a retired slot is frozen (zero right-hand side, converged) until it is admitted again
-__global__ void k_col_free(int nu, int K, int c, double *sc, double *B, double *R, double *X, double *P) {
+__global__ void k_col_free(int nu, int K, int c, double *sc, double *B, double *R, double *X, double *P, float *rb32,
+                           int64_t off32) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nu) {
         int64_t e = (int64_t)i * K + c;
         B[e] = 0.0;
         R[e] = 0.0;
+        if (rb32 && e >= off32) rb32[e - off32] = 0.0f;
         X[e] = 0.0;
         P[e] = 0.0;
     }
@@ -1328,7 +1349,8 @@ int vemg_engine_admit(vemg_engine *e, const double *b_dev, double rtol, int max_
         VEMG_CHECK_LAUNCH();
         k_col_admit<<<1, 1, 0, s>>>(0, neu, 1.0 / nu, K, c, e->colpart, W->sc, rtol, max_it);
         VEMG_CHECK_LAUNCH();
-        k_col_prepare<<<grid_for(nu, 256), 256, 0, s>>>(nu, K, c, W->sc, W->B, W->R, W->X, W->P, W->Z, W->Q);
+        k_col_prepare<<<grid_for(nu, 256), 256, 0, s>>>(nu, K, c, W->sc, W->B, W->R, W->X, W->P, W->Z, W->Q, W->Rb32,
+                                                        rb32_offset(h, W));
         VEMG_CHECK_LAUNCH();
         k_col_sum<<<kColBlocks, 256, 0, s>>>(nu, K, c, W->B, 1, e->colpart);
         VEMG_CHECK_LAUNCH();
@@ -1431,7 +1453,8 @@ int vemg_engine_retire(vemg_engine *e, int slot, double *x_dev) {
         k_col_scatter<<<grid_for(std::max(nu, ntop), 256), 256, 0, s>>>(nu, K, slot, neu, W->caller_of, h->tops, ntop,
                                                                          W->sc, W->X, x_dev);
         VEMG_CHECK_LAUNCH();
-        k_col_free<<<grid_for(nu, 256), 256, 0, s>>>(nu, K, slot, W->sc, W->B, W->R, W->X, W->P);
+        k_col_free<<<grid_for(nu, 256), 256, 0, s>>>(nu, K, slot, W->sc, W->B, W->R, W->X, W->P, W->Rb32,
+                                                     rb32_offset(h, W));
         VEMG_CHECK_LAUNCH();
         VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
         h->launches += neu ? 4 : 2;
