@@ -129,7 +129,9 @@ static double *gsc(BatchWork *w) { return w->sc + B_COUNT * w->K; }
 // ------------------------------------------------------------------------------------------
 // batched CSR row operations (natural order)
 
-enum { BOP_SPMV = 0, BOP_SPMV_ADD = 1, BOP_SOR = 2, BOP_RES = 3 };
+// BOP_SPMV_PLUS: y = b_part + A x, where rows r >= cur start from b[(r - cur) K + c] (and the
+// others from 0): z = [0; x_bar] + E~ y_s formed in the accumulator type, converted once
+enum { BOP_SPMV = 0, BOP_SPMV_ADD = 1, BOP_SOR = 2, BOP_RES = 3, BOP_SPMV_PLUS = 4 };
 
 __global__ void k_bto_float(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
     pdl_begin();
@@ -175,7 +177,10 @@ __global__ void __launch_bounds__(32 * kMaxWarps) k_bcsr(int nrows, const int *_
     for (int c0 = gl; c0 < K; c0 += kCpl * KW) {
         AT acc[kCpl];
 #pragma unroll
-        for (int u = 0; u < kCpl; ++u) acc[u] = 0;
+        for (int u = 0; u < kCpl; ++u)
+            acc[u] = (OP == BOP_SPMV_PLUS && valid && r >= cur && c0 + u * KW < K)
+                         ? (AT)b[(int64_t)(r - cur) * K + c0 + u * KW]
+                         : (AT)0;
         if (!skip_all) {
             for (int k0 = 0; k0 < wmax; k0 += KW) {
                 int k = k0 + gl;
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(32 * kMaxWarps) k_bcsr(int nrows, const int *_
             const int c = c0 + u * KW;
             if (c >= K) continue;
             int64_t e = (int64_t)r * K + c;
-            if (OP == BOP_SPMV) y[e] = (YT)acc[u];
+            if (OP == BOP_SPMV || OP == BOP_SPMV_PLUS) y[e] = (YT)acc[u];
             else if (OP == BOP_SPMV_ADD) y[e] = (YT)((AT)y[e] + acc[u]);
             else if (OP == BOP_SOR) y[e] = (YT)(((AT)b[e] - acc[u]) * (AT)dg[r]);
             else y[e] = (YT)((AT)b[e] - acc[u]);
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(32 * kMaxWarps) k_bcsr_narrow(int nrows, const
     int lo = A.rp[r], hi = A.rp[r + 1];
     const VT *v = (const VT *)A.v;
     pdl_begin();
-    AT acc = 0;
+    AT acc = (OP == BOP_SPMV_PLUS && r >= cur) ? (AT)b[(int64_t)(r - cur) * K + c] : (AT)0;
     if (!(OP == BOP_SOR && cur == 0)) {
         for (int k0 = lo; k0 < hi; k0 += kBU) {
             int cc[kBU];
@@ -250,7 +255,7 @@ __global__ void __launch_bounds__(32 * kMaxWarps) k_bcsr_narrow(int nrows, const
         }
     }
     int64_t e = (int64_t)r * K + c;
-    if (OP == BOP_SPMV) y[e] = (YT)acc;
+    if (OP == BOP_SPMV || OP == BOP_SPMV_PLUS) y[e] = (YT)acc;
     else if (OP == BOP_SPMV_ADD) y[e] = (YT)((AT)y[e] + acc);
     else if (OP == BOP_SOR) y[e] = (YT)(((AT)b[e] - acc) * (AT)dg[r]);
     else y[e] = (YT)((AT)b[e] - acc);
@@ -673,17 +678,19 @@ static void bprecond(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
             bvcycle<XT, double>(*W->bbar, W, 1, 0, W->R + (int64_t)mt * K, xb, s);
         }
         VEMG_CHECK_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
-        // z = E~ y_s + [0; x_bar] (in FP32 with FP32 V-cycles, converted once into the FP64 z)
-        if (std::is_same<XT, float>::value && W->Ev32)
-            bcsr<BOP_SPMV, float, XT, double, double, float>(CsrP{h->E.rp, h->E.ci, W->Ev32}, h->n, nullptr, 0,
-                                                            (const float *)nullptr, (const double *)nullptr, x0,
-                                                            W->Z, K, nullptr, -1, s, 2);
-        else
+        // z = E~ y_s + [0; x_bar]: with FP32 V-cycles formed in FP32 from x_bar on and converted
+        // once into the FP64 z; with FP64 ones in FP64
+        if (std::is_same<XT, float>::value && W->Ev32) {
+            bcsr<BOP_SPMV_PLUS, float, XT, XT, double, float>(CsrP{h->E.rp, h->E.ci, W->Ev32}, h->n, nullptr, 0,
+                                                             (const float *)nullptr, (const XT *)xb, x0, W->Z, K,
+                                                             nullptr, mt, s, 2);
+        } else {
             bcsr<BOP_SPMV, double, XT, double, double, double>(CsrP{h->E.rp, h->E.ci, h->E.v}, h->n, nullptr, 0,
                                                                (const double *)nullptr, (const double *)nullptr, x0,
                                                                W->Z, K, nullptr, -1, s, 2);
-        pdl_launch(k_badd<XT>, grid_for(nbk, 256), 256, s, nbk, (const XT *)xb, W->Z + (int64_t)mt * K, 0);
-        BATCH_LAUNCHED();
+            pdl_launch(k_badd<XT>, grid_for(nbk, 256), 256, s, nbk, (const XT *)xb, W->Z + (int64_t)mt * K, 0);
+            BATCH_LAUNCHED();
+        }
     } else {
         bvcycle<XT, double>(*W->bbar, W, 1, 0, W->R, xb, s);
         int64_t N = (int64_t)h->nu * K;
