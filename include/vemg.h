@@ -180,7 +180,9 @@ int vemg_solve(vemg_hierarchy *h, const double *b_dev, double *x_dev, double rto
                vemg_info *info, void *stream);
 
 /* As vemg_solve with HOST arrays b_host and x_host (n_nodes doubles, caller order): copies b to
-   the device, solves, copies x back. Page-locked host memory gives asynchronous copies. */
+   the device, solves, copies x back. Page-locked host memory gives asynchronous copies. The first
+   call allocates two device vectors of n_nodes doubles that stay with the hierarchy (counted by
+   vemg_hierarchy_bytes), so later calls allocate nothing. */
 int vemg_solve_host(vemg_hierarchy *h, const double *b_host, double *x_host, double rtol, int max_it,
                     vemg_info *info, void *stream);
 

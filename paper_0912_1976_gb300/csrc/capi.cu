@@ -374,10 +374,13 @@ int vemg_solve_host(vemg_hierarchy *h, const double *b_host, double *x_host, dou
     return guarded([&] {
         if (!h || !b_host || !x_host || !(rtol >= 0.0) || max_it < 0) return VEMG_EINVAL;
         cudaStream_t s = (cudaStream_t)stream;
-        Scratch<double> bd(h->n), xd(h->n);
-        VEMG_CHECK_CUDA(cudaMemcpyAsync(bd, b_host, sizeof(double) * h->n, cudaMemcpyHostToDevice, s));
-        int rc = solve(h, bd, xd, rtol, max_it, info, s);
-        VEMG_CHECK_CUDA(cudaMemcpyAsync(x_host, xd, sizeof(double) * h->n, cudaMemcpyDeviceToHost, s));
+        if (!h->host_b) {   // kept with the hierarchy: no allocation (nor its device-wide free) per call
+            h->host_b = h->arena.alloc<double>(h->n);
+            h->host_x = h->arena.alloc<double>(h->n);
+        }
+        VEMG_CHECK_CUDA(cudaMemcpyAsync(h->host_b, b_host, sizeof(double) * h->n, cudaMemcpyHostToDevice, s));
+        int rc = solve(h, h->host_b, h->host_x, rtol, max_it, info, s);
+        VEMG_CHECK_CUDA(cudaMemcpyAsync(x_host, h->host_x, sizeof(double) * h->n, cudaMemcpyDeviceToHost, s));
         VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
         return rc;
     });

@@ -256,6 +256,7 @@ struct vemg_hierarchy {
     int precond = VEMG_PRECOND_ADDITIVE;
     // Krylov work vectors (internal order, length n)
     double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *b = nullptr;
+    double *host_b = nullptr, *host_x = nullptr;  // device copies of vemg_solve_host's buffers (caller order)
     float *rf = nullptr, *zf = nullptr;           // mixed precision preconditioner input / output
     double *red = nullptr;                        // reduction partials
     double *scal = nullptr;                       // device scalars
