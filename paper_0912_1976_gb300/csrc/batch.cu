@@ -27,8 +27,10 @@ static constexpr int kBU = 8;          // entries loaded per round trip in a bat
 static constexpr int kMaxK = 128;      // widest batch
 static constexpr int kSellWarps = 4;   // warps per block of the batched row kernels (untuned default)
 static constexpr int kMaxWarps = 8;    // most warps per block the autotuner tries
-// columns a lane of a batched row kernel takes per pass: 8 with FP32 accumulators, 4 with FP64
-// ones (8 FP64 accumulators spill)
+// columns a lane of a batched row kernel takes per pass when the batch is wide enough (K >= that
+// many times the lanes per row): 8 with FP32 accumulators, 4 with FP64 ones (8 FP64 accumulators
+// spill). Narrower batches take one column per pass: unused accumulator slots cost registers and
+// code size, which slowed the 8-column engines of the serving stream by about 2x.
 template <class AT>
 __host__ __device__ constexpr int cols_per_lane() { return sizeof(AT) == 4 ? 8 : 4; }
 
@@ -142,7 +144,7 @@ __global__ void k_bto_float(int64_t n, const double *__restrict__ a, float *__re
 // Rows idx in [0, nrows): row = rows ? rows[idx] : r0 + idx, a group of KW lanes per row, columns
 // c = lane % KW + j KW. SOR skips the diagonal entry and, when sweeping from x = 0 (cur >= 0), every
 // entry whose column has colour >= cur (not yet visited: zero). RES keeps the diagonal: y = b - A x.
-template <int OP, class VT, class XT, class BT, class YT, class AT, int KW>
+template <int OP, class VT, class XT, class BT, class YT, class AT, int KW, int CPL>
 __global__ void __launch_bounds__(32 * kMaxWarps) k_bcsr(int nrows, const int *__restrict__ rows, int r0, CsrP A,
                                                          const VT *__restrict__ dg, const BT *__restrict__ b,
                                                          const XT *x, YT *y, int K, const int *__restrict__ colour,
@@ -170,17 +172,15 @@ __global__ void __launch_bounds__(32 * kMaxWarps) k_bcsr(int nrows, const int *_
         if (OP == BOP_SOR && cc0 >= 0 && (cc0 == r || (cur > 0 && __ldg(colour + cc0) >= cur))) cc0 = -1;
     }
     pdl_begin();
-    // a lane takes the columns c0, c0 + KW, ..., kCpl of them per pass, so that each entry of the
-    // row issues kCpl independent loads of its neighbour's x row. K and KW are powers of two, so
+    // a lane takes the columns c0, c0 + KW, ..., CPL of them per pass, so that each entry of the
+    // row issues CPL independent loads of its neighbour's x row. K, KW and CPL are powers of two
+    // and K is a multiple of CPL * KW (or CPL = 1), so every column c0 + u KW of a pass exists and
     // every lane of the warp makes the same number of passes (the shuffles need all 32).
-    constexpr int kCpl = cols_per_lane<AT>();
-    for (int c0 = gl; c0 < K; c0 += kCpl * KW) {
-        AT acc[kCpl];
+    for (int c0 = gl; c0 < K; c0 += CPL * KW) {
+        AT acc[CPL];
 #pragma unroll
-        for (int u = 0; u < kCpl; ++u)
-            acc[u] = (OP == BOP_SPMV_PLUS && valid && r >= cur && c0 + u * KW < K)
-                         ? (AT)b[(int64_t)(r - cur) * K + c0 + u * KW]
-                         : (AT)0;
+        for (int u = 0; u < CPL; ++u)
+            acc[u] = (OP == BOP_SPMV_PLUS && valid && r >= cur) ? (AT)b[(int64_t)(r - cur) * K + c0 + u * KW] : (AT)0;
         if (!skip_all) {
             for (int k0 = 0; k0 < wmax; k0 += KW) {
                 int k = k0 + gl;
@@ -200,8 +200,7 @@ __global__ void __launch_bounds__(32 * kMaxWarps) k_bcsr(int nrows, const int *_
                         if (cj >= 0) {
                             const XT *xr = x + (int64_t)cj * K;
 #pragma unroll
-                            for (int u = 0; u < kCpl; ++u)
-                                if (c0 + u * KW < K) acc[u] += (AT)vj * (AT)xr[c0 + u * KW];
+                            for (int u = 0; u < CPL; ++u) acc[u] += (AT)vj * (AT)xr[c0 + u * KW];
                         }
                     }
                 }
@@ -209,9 +208,8 @@ __global__ void __launch_bounds__(32 * kMaxWarps) k_bcsr(int nrows, const int *_
         }
         if (!valid) continue;
 #pragma unroll
-        for (int u = 0; u < kCpl; ++u) {
+        for (int u = 0; u < CPL; ++u) {
             const int c = c0 + u * KW;
-            if (c >= K) continue;
             int64_t e = (int64_t)r * K + c;
             if (OP == BOP_SPMV || OP == BOP_SPMV_PLUS) y[e] = (YT)acc[u];
             else if (OP == BOP_SPMV_ADD) y[e] = (YT)((AT)y[e] + acc[u]);
@@ -285,11 +283,25 @@ static void bcsr(CsrP A, int nrows, const int *rows, int r0, const VT *dg, const
     int RW = 32 / KW;
     int64_t warps = (nrows + RW - 1) / RW;
     int grid = (int)((warps + wpb - 1) / wpb);
+    constexpr int C = cols_per_lane<AT>();
+    const bool wide = K >= C * KW;   // then K is a multiple of C * KW (both powers of two)
     switch (KW) {
-        case 4: pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 4>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
-        case 8: pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 8>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
-        case 16: pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 16>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
-        default: pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 32>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur); break;
+        case 4:
+            if (wide) pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 4, C>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+            else pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 4, 1>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+            break;
+        case 8:
+            if (wide) pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 8, C>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+            else pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 8, 1>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+            break;
+        case 16:
+            if (wide) pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 16, C>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+            else pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 16, 1>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+            break;
+        default:
+            if (wide) pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 32, C>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+            else pdl_launch(k_bcsr<OP, VT, XT, BT, YT, AT, 32, 1>, grid, blk, s, nrows, rows, r0, A, dg, b, x, y, K, colour, cur);
+            break;
     }
     BATCH_LAUNCHED();
 }
