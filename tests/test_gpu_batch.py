@@ -131,3 +131,21 @@ def test_batched_columns_match_the_oracle_above_a_million_nodes():
         assert infos[c]["true_relres"] <= 2e-8
     record("batched_vs_oracle_1M", n=m.n, worst_rel_l2=worst, iters=[i["iters"] for i in infos])
     h.destroy()
+
+
+@pytest.mark.parametrize("precision", [V.VEMG_PREC_FP64, V.VEMG_PREC_FP32])
+def test_wide_batch_results_do_not_depend_on_columns_per_pass(precision):
+    """Width 64: 4 or 8 lanes per row take several columns per pass (8 with FP32 accumulators, 4
+    with FP64 ones), 16 or 32 lanes one column per pass. Each column's products are added in the
+    same order either way: the same iterations and the same bits."""
+    m, vm, A, h = _setup(precision=precision)
+    B = _rhs(m.n, 40, 700)                    # batch width 64
+    out = []
+    for kw, wp in ((4, 4), (8, 2), (16, 8), (32, 4)):
+        V.vemg_batch_set_tuning(h, 64, [kw] * 3, [wp] * 3)
+        X, infos = V.vemg_solve_batch(h, B, rtol=1e-9, max_it=300)
+        assert all(i["status"] == "OK" for i in infos)
+        out.append((X.clone(), [i["iters"] for i in infos]))
+    for X, it in out[1:]:
+        assert it == out[0][1]
+        assert torch.equal(X, out[0][0])
