@@ -108,7 +108,7 @@ typedef struct vemg_options {
     int precision;    /* VEMG_PREC_FP64, VEMG_PREC_FP32 or VEMG_PREC_BF16 */
     double strength;  /* SA strong-coupling threshold, section 6: 0.01 */
     double omega_p;   /* SA prolongator smoothing weight, section 6: 2/3 */
-    int coarse_max;   /* a level of at most this many rows is solved directly (dense) */
+    int coarse_max;   /* a level of at most this many rows is solved directly (dense), 1..1024 */
     int max_levels;   /* per multigrid chain, at most 16 */
     int precond;      /* VEMG_PRECOND_*. With Dirichlet-top the additive form and SA are the same
                          cycle (SA on A_bar); VL_SOR needs Neumann (VEMG_EINVAL otherwise) */
@@ -139,7 +139,7 @@ typedef struct vemg_info {
 typedef struct vemg_hierarchy vemg_hierarchy;
 
 /* Fill opts with the paper's parameters (section 6): strength 0.01, omega_p = 2/3, Neumann,
-   FP64, coarse_max = 512, max_levels = 10, the additive preconditioner, VEMG_CYCLE_AUTO,
+   FP64, coarse_max = 1024, max_levels = 10, the additive preconditioner, VEMG_CYCLE_AUTO,
    tail_rows = 0, surf_nullspace = 1, tail_cluster = 0. */
 void vemg_default_options(vemg_options *opts);
 

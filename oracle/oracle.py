@@ -26,7 +26,8 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ENOTCONV", 5: "EBRE
 # the paper's smoothed-aggregation parameters (section 6)
 THETA = 0.01
 OMEGA_P = 2.0 / 3.0
-COARSE_MAX = 512
+# the size of a directly solved coarsest level and the level cap: the paper states neither
+COARSE_MAX = 1024
 MAX_LEVELS = 10
 
 

@@ -156,7 +156,7 @@ void vemg_default_options(vemg_options *o) {
     o->precision = VEMG_PREC_FP64;
     o->strength = 0.01;
     o->omega_p = 2.0 / 3.0;
-    o->coarse_max = 512;
+    o->coarse_max = 1024;
     o->max_levels = 10;
     o->precond = VEMG_PRECOND_ADDITIVE;
     o->cycle = VEMG_CYCLE_AUTO;

@@ -57,7 +57,7 @@ def test_host_argument_checks_without_gpu():
     assert o.strength == 0.01 and o.omega_p == 2.0 / 3.0 and o.bc == V.VEMG_NEUMANN
     # every field as the C side fills it (a layout mismatch of the ctypes mirror shows here)
     assert (o.precision, o.coarse_max, o.max_levels, o.precond, o.cycle, o.tail_rows, o.surf_nullspace,
-            o.tail_cluster) == (V.VEMG_PREC_FP64, 512, 10, V.VEMG_PRECOND_ADDITIVE, V.VEMG_CYCLE_AUTO, 0, 1, 0)
+            o.tail_cluster) == (V.VEMG_PREC_FP64, 1024, 10, V.VEMG_PRECOND_ADDITIVE, V.VEMG_CYCLE_AUTO, 0, 1, 0)
     L.vemg_destroy(None)
 
 

@@ -63,7 +63,11 @@ def test_cycle_equals_oracle_with_rounded_operators(name, pc):
         # the rounding itself moves the cycle by a few times BF16's unit roundoff (2^-9)
         d_fp64 = np.linalg.norm(v - v64) / np.linalg.norm(v64)
         assert d_round <= 1e-4, (c, d_round)
-        assert d_fp64 >= 10 * d_round and d_fp64 <= 5e-2, (c, d_fp64, d_round)
+        if V.vemg_get_size(h, "nlev", c) > 1:
+            assert d_fp64 >= 10 * d_round and d_fp64 <= 5e-2, (c, d_fp64, d_round)
+        else:
+            # a chain that is one dense level: its inverse keeps its precision, nothing is rounded
+            assert d_fp64 <= 1e-4, (c, d_fp64)
     r = rng.standard_normal(om.n)
     z = V.vemg_precond(h, torch.from_numpy(r).cuda()).cpu().numpy()
     zo = om.precond(r)

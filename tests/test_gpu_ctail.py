@@ -16,10 +16,10 @@ pytestmark = pytest.mark.gpu
 
 MESHES = {
     # A_bar chain 128,960 -> 36,537 -> 11,079 -> 4,030 (coarsening stalls there: the last level is
-    # swept, not inverted), surface chain 4,030 -> 585 -> 40 (dense)
+    # swept, not inverted), surface chain 4,030 -> 585 (dense)
     "zjit64": lambda: I.make_mesh(64, 61, 32, I.depth_sines(1e-3), z_jitter=0.3, seed=9),
-    # A_bar 12,276 -> 3,634 -> 1,023 -> 94 (dense), surface 1,023 -> 170: a tail that is only the
-    # dense coarsest level
+    # A_bar 12,276 -> 3,634 -> 1,023 (dense), surface 1,023 (dense): a tail that is only the dense
+    # coarsest level
     "clust32": lambda: I.make_mesh(32, 30, 12, I.depth_sines(1e-3), z_jitter=0.3, seed=10, cluster=0.9),
 }
 _cache = {}
