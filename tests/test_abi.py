@@ -51,6 +51,8 @@ def test_host_argument_checks_without_gpu():
     assert L.vemg_hierarchy_bytes(None, None) == V.VEMG_EINVAL
     assert L.vemg_set_allocator(C.c_void_p(1), None, None) == V.VEMG_EINVAL
     assert L.vemg_set_allocator(None, None, None) == V.VEMG_OK
+    busy = C.c_int(7)
+    assert L.vemg_engine_query(None, C.byref(busy)) == V.VEMG_EINVAL and busy.value == 7
     for code in range(9):
         assert V.vemg_strerror(code).startswith("VEMG_")
     o = V.vemg_default_options()

@@ -32,6 +32,29 @@ def _run_until_done(eng, slots, max_steps=500):
     raise AssertionError("engine did not finish")
 
 
+def test_engine_query_polls_without_waiting():
+    """vemg_engine_query reports work still enqueued on the engine's stream (behind a kernel that
+    spins ~25 ms) without waiting for it, and idle once the stream has drained; the slot states
+    it then exposes are those after the step."""
+    m, vm, A, h = _hier(V.VEMG_PREC_FP64, V.VEMG_NEUMANN)
+    eng = V.Engine(h, 2)
+    b = torch.from_numpy(I.normal_loads(m.n, 90)).cuda()
+    s = eng.admit(b, rtol=1e-9)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(eng.stream):
+        torch.cuda._sleep(50_000_000)
+    eng.launch(1)
+    assert not eng.query()                 # the spin is still ahead of the step
+    eng.wait()
+    assert eng.query()
+    st, info = eng.poll(s)
+    assert st == V.VEMG_SLOT_RUNNING and info["iters"] >= 1
+    _run_until_done(eng, [s])
+    x = torch.empty_like(b)
+    eng.retire(s, x)
+    assert eng.query()
+
+
 @pytest.mark.parametrize("precision", [V.VEMG_PREC_FP64, V.VEMG_PREC_FP32])
 @pytest.mark.parametrize("bc", [V.VEMG_NEUMANN, V.VEMG_DIRICHLET_TOP])
 def test_engine_slots_equal_single_solves(precision, bc):
