@@ -80,3 +80,24 @@ def test_batched_workload_columns_match_oracle():
            iters=[infos[c]["iters"] for c in (0, 37)])
     h.destroy()
     A.free()
+
+
+def test_unstructured_workload_dirichlet_top_matches_oracle():
+    """The Dirichlet-top variant of the same workload (the A_bar chain alone), converged."""
+    m = I.make_workload_mesh("xyjit192")
+    vm = V.Mesh.from_inputs(m)
+    A = V.vemg_assemble(vm)
+    h = V.vemg_setup(A, vm, V.vemg_default_options(bc=V.VEMG_DIRICHLET_TOP, precision=V.VEMG_PREC_FP64))
+    om = O.Problem(m, bc=O.BC_DIRICHLET_TOP, openmp=True)
+    b = I.normal_loads(m.n, 2000)
+    xg, ig = V.vemg_solve(h, torch.from_numpy(b).cuda(), rtol=1e-8, max_it=1000)
+    ro = om.solve(b, tol=1e-8, maxit=1000)
+    err = _rel(xg.cpu().numpy(), ro["x"])
+    record("config3_dirichlet_full_size_vs_oracle", iters_gpu=ig["iters"], iters_oracle=ro["iters"], rel_l2=err,
+           true_relres_gpu=ig["true_relres"])
+    assert ig["status"] == "OK" and ro["status"] == "OK"
+    assert abs(ig["iters"] - ro["iters"]) <= 1
+    assert ig["true_relres"] <= 2e-8
+    assert err <= 1e-8, err
+    h.destroy()
+    A.free()
