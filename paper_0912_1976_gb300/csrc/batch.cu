@@ -1,3 +1,4 @@
+#include <vector>
 // batch.cu -- many right-hand sides in one solve.
 //
 // K systems A x_c = b_c share one hierarchy. Vectors are interleaved (row-major n x K, K a power
@@ -86,8 +87,8 @@ struct CsrP {
 };
 
 struct BatchGraphs {
-    cudaGraph_t gpre = nullptr, gloop = nullptr, gpost = nullptr;
-    cudaGraphExec_t pre = nullptr, loop = nullptr, post = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle handle = 0;
     int64_t k_pre = 0, k_body = 0, k_post = 0;
 };
@@ -814,12 +815,8 @@ static void bphase_post(vemg_hierarchy *h, BatchWork *W, cudaStream_t s) {
 static void release_batch_graphs(BatchWork *W) {
     BatchGraphs *G = W->graphs;
     if (!G) return;
-    if (G->pre) cudaGraphExecDestroy(G->pre);
-    if (G->loop) cudaGraphExecDestroy(G->loop);
-    if (G->post) cudaGraphExecDestroy(G->post);
-    if (G->gpre) cudaGraphDestroy(G->gpre);
-    if (G->gloop) cudaGraphDestroy(G->gloop);
-    if (G->gpost) cudaGraphDestroy(G->gpost);
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->g) cudaGraphDestroy(G->g);
     delete G;
     W->graphs = nullptr;
 }
@@ -833,43 +830,43 @@ static void build_batch_graphs(vemg_hierarchy *h, BatchWork *W) {
     int64_t count = 0;
     b_count = &count;
     try {
-        VEMG_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        // one graph per solve: the preparation and the kernel that sets the loop condition, a
+        // WHILE node whose body is one iteration of every column, then the exit work
+        VEMG_CHECK_CUDA(cudaGraphCreate(&G->g, 0));
+        VEMG_CHECK_CUDA(cudaGraphConditionalHandleCreate(&G->handle, G->g, 0, cudaGraphCondAssignDefault));
+        VEMG_CHECK_CUDA(cudaStreamBeginCaptureToGraph(cs, G->g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         bphase_pre(h, W, cs);
-        VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &G->gpre));
-        G->k_pre = count;
-        count = 0;
-        VEMG_CHECK_CUDA(cudaGraphCreate(&G->gloop, 0));
-        VEMG_CHECK_CUDA(cudaGraphConditionalHandleCreate(&G->handle, G->gloop, 0, cudaGraphCondAssignDefault));
-        VEMG_CHECK_CUDA(cudaStreamBeginCaptureToGraph(cs, G->gloop, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         k_bcond_init<<<1, 1, 0, cs>>>(gsc(W), G->handle);
         BATCH_LAUNCHED();
-        cudaGraph_t captured = G->gloop;
+        G->k_pre = count;
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        VEMG_CHECK_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &deps, nullptr, &ndeps));
+        std::vector<cudaGraphNode_t> frontier(deps, deps + ndeps);
+        cudaGraph_t captured = G->g;
         VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &captured));
-        cudaGraphNode_t init_node;
-        size_t nn = 1;
-        VEMG_CHECK_CUDA(cudaGraphGetNodes(G->gloop, &init_node, &nn));
         cudaGraphNodeParams cp = {};
         cp.type = cudaGraphNodeTypeConditional;
         cp.conditional.handle = G->handle;
         cp.conditional.type = cudaGraphCondTypeWhile;
         cp.conditional.size = 1;
         cudaGraphNode_t cnode;
-        VEMG_CHECK_CUDA(cudaGraphAddNode(&cnode, G->gloop, &init_node, nullptr, 1, &cp));
+        VEMG_CHECK_CUDA(cudaGraphAddNode(&cnode, G->g, frontier.data(), nullptr, frontier.size(), &cp));
         cudaGraph_t body = cp.conditional.phGraph_out[0];
+        count = 0;
         VEMG_CHECK_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         bphase_direction(h, W, cs);
         bphase_step(h, W, cs, G->handle, 1);
         VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &body));
-        G->k_body = count - 1;   // k_bcond_init runs once per solve
-        G->k_pre += 1;
+        G->k_body = count;
         count = 0;
-        VEMG_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        VEMG_CHECK_CUDA(cudaStreamBeginCaptureToGraph(cs, G->g, &cnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
         bphase_post(h, W, cs);
-        VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &G->gpost));
+        captured = G->g;
+        VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &captured));
         G->k_post = count;
-        VEMG_CHECK_CUDA(cudaGraphInstantiate(&G->pre, G->gpre, 0));
-        VEMG_CHECK_CUDA(cudaGraphInstantiate(&G->loop, G->gloop, 0));
-        VEMG_CHECK_CUDA(cudaGraphInstantiate(&G->post, G->gpost, 0));
+        VEMG_CHECK_CUDA(cudaGraphInstantiate(&G->exec, G->g, 0));
     } catch (...) {
         cudaStreamDestroy(cs);
         b_count = saved;
@@ -1110,9 +1107,7 @@ int solve_batch(vemg_hierarchy *h, int k, const double *Bin, int64_t ldb, double
     if (!W->graphs) build_batch_graphs(h, W);
     BatchGraphs *G = W->graphs;
     if (use_graph) {
-        VEMG_CHECK_CUDA(cudaGraphLaunch(G->pre, s));
-        VEMG_CHECK_CUDA(cudaGraphLaunch(G->loop, s));
-        VEMG_CHECK_CUDA(cudaGraphLaunch(G->post, s));
+        VEMG_CHECK_CUDA(cudaGraphLaunch(G->exec, s));   // the whole batched solve, one launch
     } else {
         bphase_pre(h, W, s);
         for (;;) {

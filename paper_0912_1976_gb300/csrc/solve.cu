@@ -1,3 +1,4 @@
+#include <vector>
 // solve.cu -- the solve phase: preconditioned CG with the additive vertical-extrapolation
 // multigrid preconditioner (Kramer, Cotter and Pain, section 5.5, Eq. ourpreconditioner):
 //
@@ -877,8 +878,8 @@ __global__ void k_cond_init(const double *sc, cudaGraphConditionalHandle handle)
 // the iteration, shared by the plain stream path and graph capture
 
 struct Graphs {
-    cudaGraph_t gpre = nullptr, gloop = nullptr, gpost = nullptr;
-    cudaGraphExec_t pre = nullptr, loop = nullptr, post = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle handle = 0;
     int64_t k_pre = 0, k_body = 0, k_post = 0;
 };
@@ -947,48 +948,46 @@ static void build_graphs(vemg_hierarchy *h) {
     int64_t count = 0;
     g_count = &count;
     try {
-        // first iteration
-        VEMG_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        // One graph per solve: the first iteration and the kernel that sets the loop condition,
+        // then a WHILE node whose body is one further iteration, then the exit work.
+        VEMG_CHECK_CUDA(cudaGraphCreate(&G->g, 0));
+        VEMG_CHECK_CUDA(cudaGraphConditionalHandleCreate(&G->handle, G->g, 0, cudaGraphCondAssignDefault));
+        VEMG_CHECK_CUDA(cudaStreamBeginCaptureToGraph(cs, G->g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         phase_pre(h, cs);
         phase_step(h, cs, 0, 0);
-        VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &G->gpre));
-        G->k_pre = count;
-        // loop graph: a kernel that sets the condition, then the WHILE node whose body is one
-        // further iteration
-        count = 0;
-        VEMG_CHECK_CUDA(cudaGraphCreate(&G->gloop, 0));
-        VEMG_CHECK_CUDA(cudaGraphConditionalHandleCreate(&G->handle, G->gloop, 0, cudaGraphCondAssignDefault));
-        VEMG_CHECK_CUDA(cudaStreamBeginCaptureToGraph(cs, G->gloop, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         k_cond_init<<<1, 1, 0, cs>>>(h->scal, G->handle);
         SOLVE_LAUNCHED();
-        cudaGraph_t captured = G->gloop;
+        G->k_pre = count;
+        // the nodes the WHILE node follows: the capture's current frontier
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        VEMG_CHECK_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &deps, nullptr, &ndeps));
+        std::vector<cudaGraphNode_t> frontier(deps, deps + ndeps);
+        cudaGraph_t captured = G->g;
         VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &captured));
-        cudaGraphNode_t init_node;
-        size_t nn = 1;
-        VEMG_CHECK_CUDA(cudaGraphGetNodes(G->gloop, &init_node, &nn));
         cudaGraphNodeParams cp = {};
         cp.type = cudaGraphNodeTypeConditional;
         cp.conditional.handle = G->handle;
         cp.conditional.type = cudaGraphCondTypeWhile;
         cp.conditional.size = 1;
         cudaGraphNode_t cnode;
-        VEMG_CHECK_CUDA(cudaGraphAddNode(&cnode, G->gloop, &init_node, nullptr, 1, &cp));
+        VEMG_CHECK_CUDA(cudaGraphAddNode(&cnode, G->g, frontier.data(), nullptr, frontier.size(), &cp));
         cudaGraph_t body = cp.conditional.phGraph_out[0];
+        count = 0;
         VEMG_CHECK_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         phase_direction(h, cs);
         phase_step(h, cs, G->handle, 1);
         VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &body));
-        G->k_body = count - 1;   // k_cond_init runs once per solve
-        G->k_pre += 1;
-        // exit work
+        G->k_body = count;
+        // exit work, after the WHILE node
         count = 0;
-        VEMG_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        VEMG_CHECK_CUDA(cudaStreamBeginCaptureToGraph(cs, G->g, &cnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
         phase_post(h, cs);
-        VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &G->gpost));
+        captured = G->g;
+        VEMG_CHECK_CUDA(cudaStreamEndCapture(cs, &captured));
         G->k_post = count;
-        VEMG_CHECK_CUDA(cudaGraphInstantiate(&G->pre, G->gpre, 0));
-        VEMG_CHECK_CUDA(cudaGraphInstantiate(&G->loop, G->gloop, 0));
-        VEMG_CHECK_CUDA(cudaGraphInstantiate(&G->post, G->gpost, 0));
+        VEMG_CHECK_CUDA(cudaGraphInstantiate(&G->exec, G->g, 0));
     } catch (...) {
         cudaStreamDestroy(cs);
         g_probe = saved;
@@ -1004,12 +1003,8 @@ static void build_graphs(vemg_hierarchy *h) {
 void release_graphs(vemg_hierarchy *h) {
     Graphs *G = h->graphs;
     if (G) {
-        if (G->pre) cudaGraphExecDestroy(G->pre);
-        if (G->loop) cudaGraphExecDestroy(G->loop);
-        if (G->post) cudaGraphExecDestroy(G->post);
-        if (G->gpre) cudaGraphDestroy(G->gpre);
-        if (G->gloop) cudaGraphDestroy(G->gloop);
-        if (G->gpost) cudaGraphDestroy(G->gpost);
+        if (G->exec) cudaGraphExecDestroy(G->exec);
+        if (G->g) cudaGraphDestroy(G->g);
         delete G;
         h->graphs = nullptr;
     }
@@ -1068,9 +1063,7 @@ int solve(vemg_hierarchy *h, const double *b_in, double *x_out, double rtol, int
     if (use_graph) {
         if (!h->graphs) build_graphs(h);
         Graphs *G = h->graphs;
-        VEMG_CHECK_CUDA(cudaGraphLaunch(G->pre, s));
-        VEMG_CHECK_CUDA(cudaGraphLaunch(G->loop, s));
-        VEMG_CHECK_CUDA(cudaGraphLaunch(G->post, s));
+        VEMG_CHECK_CUDA(cudaGraphLaunch(G->exec, s));   // the whole solve, one launch
         VEMG_CHECK_CUDA(cudaMemcpyAsync(hs, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
         VEMG_CHECK_CUDA(cudaStreamSynchronize(s));
         int it = (int)hs[S_ITERS];
