@@ -717,13 +717,10 @@ static int64_t rb32_offset(const vemg_hierarchy *h, const BatchWork *W) {
     return single_chain(h) ? 0 : (int64_t)h->mtop * W->K;
 }
 
+// one per-column sum (the wider sums of the preconditioner step are k_bsums_zrq's)
 static void bsums(BatchWork *W, int64_t N, const BSums &d, cudaStream_t s) {
-    int nblk = stage1_blocks(N);
-    switch (d.ns) {
-        case 1: pdl_launch(k_bsums<1>, nblk, kBT, s, N, W->K, d, W->part); break;
-        case 3: pdl_launch(k_bsums<3>, nblk, kBT, s, N, W->K, d, W->part); break;
-        default: pdl_launch(k_bsums<5>, nblk, kBT, s, N, W->K, d, W->part); break;
-    }
+    if (d.ns != 1) throw Error{VEMG_EINTERNAL};
+    pdl_launch(k_bsums<1>, stage1_blocks(N), kBT, s, N, W->K, d, W->part);
     BATCH_LAUNCHED();
 }
 
