@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(kRedThreads, kRedBlocks / 152) k_spmv_pq(SellA
 }
 
 // x += alpha p, r -= alpha q; the last block sets ||r||, the iteration count and the continuation
-// test (and, inside the loop graph, the WHILE condition)
+// test (and, inside the solve graph, the WHILE condition)
 __global__ void __launch_bounds__(kRedThreads) k_update_xr(int n, const double *__restrict__ p,
                                                            const double *__restrict__ q, double *__restrict__ x,
                                                            double *__restrict__ r, double *sc, double *part,
@@ -869,7 +869,7 @@ __global__ void k_scatter_out(int nu, const int *__restrict__ caller_of, const i
     if (i < ntop) dst[tops[i]] = 0.0;
 }
 
-// entry of the loop graph: continue only if the first iteration asked for more
+// before the WHILE node of the solve graph: continue only if the first iteration asked for more
 __global__ void k_cond_init(const double *sc, cudaGraphConditionalHandle handle) {
     cudaGraphSetConditional(handle, sc[S_CONT] != 0.0 ? 1u : 0u);
 }
