@@ -374,8 +374,9 @@ int vemg_solve_host(vemg_hierarchy *h, const double *b_host, double *x_host, dou
     return guarded([&] {
         if (!h || !b_host || !x_host || !(rtol >= 0.0) || max_it < 0) return VEMG_EINVAL;
         cudaStream_t s = (cudaStream_t)stream;
-        if (!h->host_b) {   // kept with the hierarchy: no allocation (nor its device-wide free) per call
-            h->host_b = h->arena.alloc<double>(h->n);
+        if (!h->host_b || !h->host_x) {   // kept with the hierarchy: no allocation (nor its free) per call
+            double *hb = h->host_b ? h->host_b : h->arena.alloc<double>(h->n);
+            h->host_b = hb;
             h->host_x = h->arena.alloc<double>(h->n);
         }
         VEMG_CHECK_CUDA(cudaMemcpyAsync(h->host_b, b_host, sizeof(double) * h->n, cudaMemcpyHostToDevice, s));
