@@ -195,6 +195,12 @@ def test_zero_rhs_and_host_entry_point():
     xd, idv = V.vemg_solve(h, torch.from_numpy(b).cuda(), rtol=1e-9)
     assert ih["iters"] == idv["iters"]
     assert np.array_equal(xh, xd.cpu().numpy())
+    # the device copies of the host buffers stay with the hierarchy: a second call allocates
+    # nothing and gives the same bits
+    held = V.vemg_hierarchy_bytes(h)
+    xh2, ih2 = V.vemg_solve_host(h, b, rtol=1e-9)
+    assert V.vemg_hierarchy_bytes(h) == held
+    assert ih2["iters"] == ih["iters"] and np.array_equal(xh2, xh)
 
 
 def test_mesh_errors_are_reported():
