@@ -611,6 +611,41 @@ def test_vcycle_and_preconditioner_symmetric_positive():
     assert P.nlev(1) >= 2          # a real multilevel cycle, not only the direct solve
 
 
+def test_one_level_chain_cycle_is_the_exact_inverse():
+    """A chain whose finest level has at most coarse_max rows is that level alone, solved by its
+    dense inverse: the cycle of the non-singular A_bar chain solves A_bar exactly, and the cycle of
+    the singular surface chain (constants as its nullspace) returns the zero-mean solution of a
+    mean-zero right-hand side."""
+    m = _mesh(8, 4, h0=1e-2, zj=0.3, seed=9)
+    P = O.Problem(m)
+    assert P.nlev(1) == 1 and P.nlev(0) == 1
+    rng = np.random.default_rng(21)
+    Ab = P.csr("lev.A", 1, 0).toarray()
+    b = rng.standard_normal(Ab.shape[0])
+    v = P.vcycle(1, b)
+    assert np.linalg.norm(Ab @ v - b) <= 1e-12 * np.linalg.norm(b)
+    Ac = P.csr("lev.A", 0, 0).toarray()
+    bs = rng.standard_normal(Ac.shape[0])
+    bs -= bs.mean()
+    vs = P.vcycle(0, bs)
+    assert abs(vs.mean()) <= 1e-12 * np.abs(vs).max()
+    assert np.linalg.norm(Ac @ vs - bs) <= 1e-10 * np.linalg.norm(bs)
+
+
+def test_coarsening_stops_at_the_first_level_within_coarse_max():
+    """The default coarsest size (1024 rows): the A_bar chain of a 24x24x8 mesh coarsens while a
+    level has more rows and ends at the first level within the limit, solved directly. With a
+    512-row limit the same 625-row level is where coarsening stalls (none of its nodes has a strong
+    coupling, so it has no aggregate): it stays the last level and is swept, not inverted."""
+    m = _mesh(24, 8, h0=1e-3, zj=0.3, seed=9)
+    P = O.Problem(m)
+    sizes = P.level_sizes(1)
+    assert sizes[-1] <= O.COARSE_MAX < sizes[-2] and P.size("direct", 1) == 1
+    assert all(s > O.COARSE_MAX for s in sizes[:-1])
+    Q = O.Problem(m, coarse_max=512)
+    assert Q.level_sizes(1) == sizes and Q.size("direct", 1) == 0
+
+
 def test_solve_matches_dense_bordered_system():
     for zj, xyj in [(0.3, 0.0), (0.3, 0.2)]:
         m = _mesh(8, 4, h0=1e-2, zj=zj, xyj=xyj, seed=9)
