@@ -202,3 +202,47 @@ def test_engines_keep_stepping_while_a_hierarchy_builds():
     done = {r.rid: r for r in srv.run(reqs)}
     assert done[0].finished < 0.3 < done[1].finished
     assert srv.stats["builds"] == 2 and not srv.building
+
+
+def test_a_failing_build_raises_out_of_the_loop():
+    # a build error (say, the device is out of memory) ends the run with that error, after the
+    # worker thread has stopped
+    def build(key):
+        if key[0] == 1:
+            raise MemoryError("no room for this hierarchy")
+        return object(), PacedEngine(2, 2, 1), 0, 10
+
+    srv = S.Server(build, lambda key: 0, lambda: 1 << 40, lambda req, n: [(req.rid, j) for j in range(req.nrhs)],
+                   reserve=0)
+    reqs = [S.Request(0, 0, 1e-3, 0, 1, 0.0, 0), S.Request(1, 1, 1e-3, 0, 1, 0.0, 1)]
+    try:
+        srv.run(reqs)
+    except MemoryError:
+        pass
+    else:
+        raise AssertionError("the build error was swallowed")
+    assert srv._builder is None and not srv.building
+
+
+def test_bytes_of_a_running_build_stay_reserved():
+    # room for one hierarchy: while the first build runs, a second key is deferred (its bytes
+    # would not fit beside the reserved ones), then built once the first is idle and evicted
+    pool = Pool(total=1000)
+
+    def build(key):
+        time.sleep(0.05)
+        assert pool.used + 1000 <= pool.total, "oversubscribed"
+        pool.used += 1000
+        eng = PacedEngine(2, 2, 1)
+
+        class H:
+            def destroy(self_inner):
+                pool.used -= 1000
+        return H(), eng, 1000, 10
+
+    srv = S.Server(build, lambda key: 1000, pool.free, lambda req, n: [(req.rid, j) for j in range(req.nrhs)],
+                   reserve=0)
+    reqs = [S.Request(0, 0, 1e-3, 0, 1, 0.0, 0), S.Request(1, 0, 1e-2, 0, 1, 0.0, 1)]
+    done = srv.run(reqs)
+    assert len(done) == 2
+    assert srv.stats["deferred"] > 0 and srv.stats["evictions"] >= 1 and srv.stats["builds"] == 2
